@@ -1,0 +1,417 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a textbook
+exact solution, a convergence order the paper states, an invariant of the
+discrete scheme, or a special case that reduces to a textbook routine.
+Together they are chosen so that a dropped term, a wrong sign or index, or a
+transposed operand anywhere in the oracle fails at least one of them
+(``test_oracle_mutants.py`` plants such mistakes to show it).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import exact
+from paper_0910_2854_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def make_box(oracle_mod, w, **kw):
+    ob = oracle_mod.OracleBox(*w.dims, w.gamma, bc=w.bc, h=w.h, phi=w.phi, **kw)
+    ob.set_state(w.state)
+    return ob
+
+
+def run_to(ob, T, cfl=0.5):
+    t = 0.0
+    n = 0
+    while t < T - 1e-14:
+        dt = min(ob.cfl(cfl), (T - t) / 2.0)
+        ob.step(dt)
+        t += 2.0 * dt
+        n += 1
+    return n
+
+
+def read_golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+# ---------------------------------------------------------------------------
+# the exact Riemann solver itself (used as the Sod reference)
+# ---------------------------------------------------------------------------
+
+def test_exact_riemann_reproduces_toro_table():
+    g = read_golden("toro_sod_star_state.txt")
+    ps, us = exact.star_state((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4)
+    assert abs(ps - g["p_star"]) < 1e-5
+    assert abs(us - g["u_star"]) < 1e-5
+    # star densities sampled just left / right of the contact
+    r, u, p = exact.riemann_euler((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4,
+                                  np.array([us - 1e-9, us + 1e-9]))
+    assert abs(r[0] - g["rho_star_left"]) < 1e-5
+    assert abs(r[1] - g["rho_star_right"]) < 1e-5
+
+
+def test_exact_riemann_jump_conditions():
+    """Rankine-Hugoniot across the right shock and isentropy across the left
+    rarefaction of the exact solution (independent of any tabulated value)."""
+    gam = 1.4
+    L, R = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    ps, us = exact.star_state(L, R, gam)
+    cr = math.sqrt(gam * R[2] / R[0])
+    S = R[1] + cr * math.sqrt((gam + 1) / (2 * gam) * ps / R[2] + (gam - 1) / (2 * gam))
+    r2, u2, p2 = exact.riemann_euler(L, R, gam, np.array([S - 1e-9]))
+    r1, u1, p1 = R
+    # mass and momentum flux continuity in the shock frame
+    assert abs(r2[0] * (u2[0] - S) - r1 * (u1 - S)) < 1e-9
+    assert abs(r2[0] * (u2[0] - S) ** 2 + p2[0] - (r1 * (u1 - S) ** 2 + p1)) < 1e-9
+    # left rarefaction: p / rho^gamma constant and u + 2c/(gam-1) constant
+    xi = np.linspace(-1.1, us - 0.1, 7)
+    r, u, p = exact.riemann_euler(L, R, gam, xi)
+    s = p / r ** gam
+    assert np.allclose(s, 1.0, rtol=1e-12)
+    riem = u + 2 * np.sqrt(gam * p / r) / (gam - 1)
+    assert np.allclose(riem, 2 * math.sqrt(gam) / (gam - 1), rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# P-1: Sod shock tube against the exact Riemann solution
+# ---------------------------------------------------------------------------
+
+def test_sod_converges_to_exact_solution(oracle_mod):
+    errs = []
+    for n in (64, 128, 256):
+        w = W.sod(n, axis=0, ntrans=1)
+        ob = make_box(oracle_mod, w)
+        run_to(ob, 0.2)
+        assert ob.flags == 0
+        r, u, p = exact.riemann_cell_averages((1, 0, 1), (0.125, 0, 0.1), 1.4,
+                                              np.linspace(0, 1, n + 1), 0.5, 0.2)
+        errs.append(np.mean(np.abs(ob.state[0, 0, 0] - r)))
+    assert errs[0] / errs[1] > 1.6 and errs[1] / errs[2] > 1.6
+    assert errs[2] < 4e-3
+
+
+# ---------------------------------------------------------------------------
+# P-2: circularly polarised Alfven wave (Sec. 4), second order
+# ---------------------------------------------------------------------------
+
+def _alfven_error(oracle_mod, w):
+    ob = make_box(oracle_mod, w)
+    run_to(ob, 1.0)
+    assert ob.flags == 0
+    # the paper's norm: mean over cells of |u^n - u^0|, summed over components
+    return float(np.sum(np.mean(np.abs(ob.state - w.state), axis=(1, 2, 3)))), ob
+
+
+def test_alfven_wave_x_second_order(oracle_mod):
+    errs = [_alfven_error(oracle_mod, W.alfven_x(n, 1, 1))[0] for n in (32, 64, 128)]
+    order = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert order[0] > 1.8 and order[1] > 1.9, (errs, order)
+    assert errs[2] < 5e-4
+
+
+def test_alfven_wave_oblique_second_order(oracle_mod):
+    """The paper's own setup: 2-D at 30 degrees on [0,1/cos a] x [0,1/sin a]."""
+    errs = []
+    for n in (16, 32, 64):
+        e, ob = _alfven_error(oracle_mod, W.alfven_oblique(n))
+        errs.append(e)
+    order = math.log2(errs[1] / errs[2])
+    assert order > 1.8, (errs, order)
+
+
+def test_linear_fast_wave_second_order(oracle_mod):
+    """Textbook fast magnetosonic eigenmode (oblique field): after one period
+    the perturbation returns, with error falling at second order.  Exercises
+    the compressive MHD coupling (pressure, b.v energy flux, b_t advection)
+    that a circularly polarised Alfven wave leaves untouched."""
+    errs = []
+    for n in (32, 64, 128):
+        w = W.fast_wave(n)
+        ob = make_box(oracle_mod, w)
+        run_to(ob, w.meta["period"])
+        errs.append(np.sum(np.mean(np.abs(ob.state - w.state), axis=(1, 2, 3))) / w.meta["eps"])
+    assert math.log2(errs[1] / errs[2]) > 1.9, errs
+    assert errs[2] < 1e-2
+
+
+# ---------------------------------------------------------------------------
+# P-3: smooth advection, second order along every axis, identical errors
+# ---------------------------------------------------------------------------
+
+def test_entropy_wave_order_all_axes(oracle_mod):
+    res = {}
+    for ax in (0, 1, 2):
+        errs = []
+        for n in (32, 64, 128):
+            w = W.entropy_wave(n, axis=ax, ntrans=1)
+            ob = make_box(oracle_mod, w)
+            run_to(ob, 1.0)
+            errs.append(np.mean(np.abs(ob.state[0] - w.state[0])))
+        res[ax] = errs
+        assert math.log2(errs[1] / errs[2]) > 1.9
+    assert res[0] == res[1] == res[2]
+
+
+# ---------------------------------------------------------------------------
+# P-4 / P-5: conservation and div b = 0 to round-off (periodic, no gravity)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("lim", [0, 1])
+def test_conservation_and_divergence(oracle_mod, lim):
+    w = W.random_smooth(12, 10, 8, seed=3, h=(0.1, 0.07, 0.13))
+    ob = make_box(oracle_mod, w, limiter=lim)
+    d0 = ob.diag()
+    div0 = _divergence(ob)
+    dt = ob.cfl(0.5)
+    ob.step(dt, 4)
+    assert ob.flags == 0
+    d1 = ob.diag()
+    vol = np.prod(ob.h)
+    scale = np.array([np.sum(np.abs(ob.state[f])) * vol for f in range(8)])
+    assert np.all(np.abs(d1[:8] - d0[:8]) <= 1e-13 * scale), (d1[:8] - d0[:8]) / scale
+    div1 = _divergence(ob)
+    bmax = np.max(np.abs(ob.state[5:8]))
+    assert np.max(np.abs(div1 - div0)) * min(ob.h) / bmax < 1e-13
+
+
+def _divergence(ob):
+    bx, by, bz = ob.state[5], ob.state[6], ob.state[7]
+    return ((bx - np.roll(bx, 1, 2)) / ob.h[0] + (by - np.roll(by, 1, 1)) / ob.h[1]
+            + (bz - np.roll(bz, 1, 0)) / ob.h[2])
+
+
+def test_divergence_kept_under_outflow(oracle_mod):
+    """Outflow: every stored face is updated by CT with ghost fluxes, so the
+    divergence of cells whose faces are all stored keeps its initial value."""
+    w = W.random_smooth(10, 9, 8, seed=5, bc=W.BC_OUTFLOW)
+    ob = make_box(oracle_mod, w)
+    div0 = _divergence(ob)[1:, 1:, 1:]
+    ob.step(ob.cfl(0.4), 3)
+    div1 = _divergence(ob)[1:, 1:, 1:]
+    bmax = np.max(np.abs(ob.state[5:8]))
+    assert np.max(np.abs(div1 - div0)) * min(ob.h) / bmax < 1e-13
+
+
+def test_ct_leaves_fluid_and_energy_untouched(oracle_mod):
+    """During B_d every non-magnetic quantity, E included, is held constant."""
+    w = W.random_smooth(8, 7, 6, seed=1)
+    for d in range(3):
+        ob = make_box(oracle_mod, w)
+        before = ob.state.copy()
+        ob.ct(d, 0.01)
+        assert np.array_equal(ob.state[:5], before[:5])
+        assert not np.array_equal(ob.state[5:], before[5:])
+
+
+def test_fluid_leaves_field_untouched(oracle_mod):
+    w = W.random_smooth(8, 7, 6, seed=2)
+    for d in range(3):
+        ob = make_box(oracle_mod, w)
+        before = ob.state.copy()
+        ob.fluid(d, 0.01)
+        assert np.array_equal(ob.state[5:], before[5:])
+        assert not np.array_equal(ob.state[:5], before[:5])
+
+
+# ---------------------------------------------------------------------------
+# P-6: special cases
+# ---------------------------------------------------------------------------
+
+def test_uniform_state_is_bitwise_fixed_point(oracle_mod):
+    st = W.assemble(np.full((5, 6, 7), 1.3), (0.4, -0.2, 0.7), 0.9, (0.3, -0.5, 0.25), 5 / 3, 0)
+    w = W.Workload("u", st, 5 / 3, (0.1, 0.2, 0.3))
+    ob = make_box(oracle_mod, w)
+    ob.step(0.01, 3)
+    assert np.array_equal(ob.state, st)
+
+
+def _euler_rusanov_pc(u, gam, dt, h):
+    """Textbook (LeVeque) two-stage scheme with the local Lax-Friedrichs /
+    Rusanov flux for the 1-D Euler equations on a periodic grid: half step
+    with the first-order flux, full step with the first-order flux of the
+    half-step state.  Independent numpy implementation."""
+    def flux(u):
+        rho, m, E = u
+        v = m / rho
+        p = (gam - 1) * (E - 0.5 * m * v)
+        c = np.sqrt(gam * p / rho)
+        return np.array([m, m * v + p, (E + p) * v]), np.abs(v) + c
+
+    def llf(u):
+        F, s = flux(u)
+        Fr, sr = np.roll(F, -1, 1), np.roll(s, -1)
+        ur = np.roll(u, -1, 1)
+        return 0.5 * (F + Fr) - 0.5 * np.maximum(s, sr) * (ur - u)
+
+    Fh = llf(u)
+    uh = u - dt / (2 * h) * (Fh - np.roll(Fh, 1, 1))
+    Ff = llf(uh)
+    return u - dt / h * (Ff - np.roll(Ff, 1, 1))
+
+
+def test_limiter_off_reduces_to_rusanov(oracle_mod):
+    """Limiter identically zero: the TVD corrector flux collapses to the
+    first-order Rusanov / LLF flux of the predicted state."""
+    n, gam = 40, 1.4
+    x = (np.arange(n) + 0.5) / n
+    rho = 1 + 0.3 * np.sin(2 * np.pi * x)
+    v = 0.5 * np.cos(2 * np.pi * x)
+    p = 1 + 0.2 * np.sin(4 * np.pi * x)
+    z = np.zeros(n)
+    st = W.assemble(rho[None, None], (v[None, None], z[None, None], z[None, None]), p[None, None],
+                    (z[None, None],) * 3, gam, 0)
+    w = W.Workload("e", st, gam, (1.0 / n, 1.0, 1.0))
+    ob = make_box(oracle_mod, w, limiter=oracle_mod.LIM_NONE)
+    dt = 0.3 / n
+    ob.fluid(0, dt)
+    u = np.array([rho, rho * v, st[4, 0, 0]])
+    ref = _euler_rusanov_pc(u, gam, dt, 1.0 / n)
+    got = np.array([ob.state[0, 0, 0], ob.state[1, 0, 0], ob.state[4, 0, 0]])
+    assert np.max(np.abs(got - ref)) < 1e-13
+
+
+def _discrete_atmosphere(n, c0=1.0, gam=5 / 3, g=2.0):
+    """Gas at rest with uniform sound speed c0 (p = c0^2 rho / gamma) in
+    phi = g x, built so that the density difference of every interface equals
+    the hydrostatic estimate of eq0321 exactly:
+    rho_{j+1} - rho_j = -(rho_j + rho_{j+1}) (phi_{j+1} - phi_j) / (2 c0^2)."""
+    h = 1.0 / n
+    x = (np.arange(n) + 0.5) * h
+    phi = g * x
+    a = g * h / (2 * c0 * c0)
+    rho = (1.0 * ((1 - a) / (1 + a)) ** np.arange(n))
+    one = np.ones((1, 1, n))
+    st = W.assemble(rho[None, None] * one, (0 * one,) * 3, (c0 * c0 / gam) * rho[None, None] * one,
+                    (0 * one,) * 3, gam, W.BC_OUTFLOW)
+    return W.Workload("atm", st, gam, (h, 1.0, 1.0), bc=W.BC_OUTFLOW, phi=phi[None, None] * one)
+
+
+def test_hse_correction_removes_hydrostatic_dissipation(oracle_mod):
+    """In a discrete hydrostatic atmosphere the HSE-corrected difference
+    delta u of the density vanishes (eq0323), so the acoustic dissipation of
+    the mass flux disappears: the density moves far less with the correction
+    than with the plain relaxation flux (eq0140).  The limiter is switched off
+    so that the first-order dissipation is not partly cancelled by the TVD
+    slopes (on an exactly geometric profile the Van Leer slopes cancel it
+    completely); what remains with the correction is the advective mass flux
+    of the small momentum imbalance."""
+    n = 32
+    w = _discrete_atmosphere(n)
+    drift = {}
+    for hse in (False, True):
+        ob = make_box(oracle_mod, w, hse=hse, limiter=oracle_mod.LIM_NONE)
+        ob.fluid(0, 0.2 / n)
+        inner = slice(4, n - 4)
+        drift[hse] = np.max(np.abs(ob.state[0, 0, 0, inner] - w.state[0, 0, 0, inner]))
+    assert drift[True] < 0.15 * drift[False], drift
+
+
+def test_free_fall_in_linear_potential(oracle_mod):
+    """Uniform gas at rest in phi = g x: interior cells follow the exact free
+    fall of one operator step, m = -rho g dt and E gains rho g^2 dt^2 / 2
+    (source of eq0254 with the sign of S_x)."""
+    n, g, dt = 16, 0.7, 0.01
+    x = (np.arange(n) + 0.5) / n
+    one = np.ones((1, 1, n))
+    st = W.assemble(one, (0 * one,) * 3, 1.0, (0 * one,) * 3, 5 / 3, W.BC_OUTFLOW)
+    phi = (g * x)[None, None] * one
+    w = W.Workload("ff", st, 5 / 3, (1.0 / n, 1.0, 1.0), bc=W.BC_OUTFLOW, phi=phi)
+    ob = make_box(oracle_mod, w)
+    ob.fluid(0, dt)
+    inner = slice(4, n - 4)
+    assert np.allclose(ob.state[1, 0, 0, inner], -g * dt, rtol=1e-13, atol=0)
+    assert np.allclose(ob.state[4, 0, 0, inner], st[4, 0, 0, inner] + 0.5 * g * g * dt * dt,
+                       rtol=1e-13, atol=0)
+    assert np.allclose(ob.state[0, 0, 0, inner], 1.0, rtol=1e-14, atol=0)
+
+
+def test_cfl_closed_form_fast_speed(oracle_mod):
+    """Fast speed limits: along b it is max(a, v_A); across b it is
+    sqrt(a^2 + v_A^2) (reading C-1); dt = k min_d h_d / (|v_d| + c_F,d)."""
+    gam, rho, p, B = 5 / 3, 2.0, 0.6, 1.1
+    a2 = gam * p / rho
+    va2 = B * B / rho
+    v = (0.3, -0.2, 0.1)
+    h = (0.05, 0.07, 0.11)
+    one = np.ones((3, 4, 5))
+    st = W.assemble(rho * one, tuple(c * one for c in v), p, (B * one, 0 * one, 0 * one), gam, 0)
+    w = W.Workload("c", st, gam, h)
+    ob = make_box(oracle_mod, w)
+    cf = [max(math.sqrt(a2), math.sqrt(va2)), math.sqrt(a2 + va2), math.sqrt(a2 + va2)]
+    ref = 0.8 * min(h[d] / (abs(v[d]) + cf[d]) for d in range(3))
+    assert abs(ob.cfl(0.8) - ref) < 1e-14 * ref
+
+
+# ---------------------------------------------------------------------------
+# P-7: axis permutation and mirror symmetry
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", ["sod", "brio_wu"])
+def test_axis_permutation_bitwise(oracle_mod, kind):
+    """A 1-D tube along x, y or z gives bitwise identical profiles with the
+    components permuted.  For an MHD tube the constraint update of the
+    transverse field comes from B_{d+1}, which sits between the two
+    d-sweeps in the x-y-z-z-y-x order for d = x, y but outside them for
+    d = z, so only x and y are compared there."""
+    outs = []
+    axes = range(3) if kind == "sod" else range(2)
+    for ax in axes:
+        w = W.sod(64, axis=ax, ntrans=1) if kind == "sod" else W.brio_wu(64, axis=ax, ntrans=1)
+        ob = make_box(oracle_mod, w, limiter=1)
+        for _ in range(10):
+            ob.step(0.2 / 64)
+        assert ob.flags == 0
+        st = ob.state.reshape(8, -1)
+        # rotate components back to the frame of the tube: (n, t1, t2)
+        perm_m = [1 + ax, 1 + (ax + 1) % 3, 1 + (ax + 2) % 3]
+        perm_b = [5 + ax, 5 + (ax + 1) % 3, 5 + (ax + 2) % 3]
+        outs.append(st[[0] + perm_m + [4] + perm_b])
+    for o in outs[1:]:
+        assert np.array_equal(outs[0], o)
+
+
+def test_mirror_symmetry_sod(oracle_mod):
+    a = make_box(oracle_mod, W.sod(64, ntrans=1))
+    b = make_box(oracle_mod, W.sod(64, ntrans=1, mirror=True))
+    for _ in range(8):
+        a.step(0.25 / 64)
+        b.step(0.25 / 64)
+    ra, rb = a.state[0, 0, 0], b.state[0, 0, 0][::-1]
+    assert np.max(np.abs(ra - rb)) < 1e-13
+    assert np.max(np.abs(a.state[1, 0, 0] + b.state[1, 0, 0][::-1])) < 1e-13
+
+
+def test_three_rotations_identity(oracle_mod):
+    """The paper's data rotation (2 pi/3 about (1,1,1), Sec. 3): the cyclic
+    relabelling (x,y,z) -> (y,z,x) applied three times is the identity, and a
+    y-sweep pair L_y B_y of a state equals the x-sweep pair L_x B_x of the
+    rotated state, rotated back."""
+    w = W.random_smooth(6, 6, 6, seed=7)
+    st = w.state
+
+    def rot(s):
+        # new x = old y, new y = old z, new z = old x; numpy order (z, y, x)
+        r = np.transpose(s, (0, 3, 1, 2))
+        return r[[0, 2, 3, 1, 4, 6, 7, 5]]
+
+    assert np.array_equal(rot(rot(rot(st))), st)
+    a = make_box(oracle_mod, w)
+    a.fluid(1, 0.01)
+    a.ct(1, 0.01)
+    b = make_box(oracle_mod, W.Workload("r", rot(st), w.gamma, w.h))
+    b.fluid(0, 0.01)
+    b.ct(0, 0.01)
+    assert np.max(np.abs(rot(a.state) - b.state)) < 1e-14
