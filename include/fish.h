@@ -1,0 +1,162 @@
+/*
+ * fish.h -- C ABI of libfish.so: FISH's operator-split ideal-MHD sweep on one
+ * GB300 GPU (Kaeppeli et al., "FISH: A 3D parallel MHD code for astrophysical
+ * applications", arXiv:0910.2854).
+ *
+ * Problem statement (Sec. 2): a box of nx*ny*nz Cartesian cells of widths
+ * dx, dy, dz; ideal gas of ratio of specific heats gamma (eq0050); cell
+ * averages u = (rho, rho v, E) (eq0070) and face averages of the magnetic
+ * field b = B/sqrt(4 pi) (eq0080-eq0080b); optional fixed gravitational
+ * potential phi (Sec. 2.3, "given and constant in time"); periodic or
+ * zeroth-order-extrapolation boundaries (Sec. 4).
+ *
+ * State layout (host and device): 8 fields of nx*ny*nz values each, one
+ * after the other, x fastest, index i + nx*(j + ny*k):
+ *   rho, m_x, m_y, m_z, E, b_x, b_y, b_z
+ * where b_x[i,j,k] is the average over the face at x_{i+1/2} (likewise b_y at
+ * y_{j+1/2}, b_z at z_{k+1/2}).  With outflow boundaries the faces at
+ * x_{-1/2}, y_{-1/2}, z_{-1/2} are ghosts (copies of the faces at +1/2).
+ *
+ * Conventions:
+ *  - Every call returns FISH_OK (0) or a FISH_ERR_* code; no exception or
+ *    exit crosses the ABI.  fish_last_error() gives a text for the last error.
+ *  - Caller-owned buffers are only read from or written to during the call;
+ *    the library owns all device memory it allocates and frees it in
+ *    fish_destroy().
+ *  - Work is queued asynchronously on the context's stream.  Device-side
+ *    errors (rho <= 0, p <= 0, NaN: reading C-16 -- no floor is applied) are
+ *    sticky per context and returned as FISH_ERR_NONPHYSICAL by the next
+ *    synchronising call (fish_cfl_dt, fish_get_state*, fish_diagnostics,
+ *    fish_sync, fish_last_dt).
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef FISH_H
+#define FISH_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fish_ctx fish_ctx;
+
+enum {
+    FISH_OK = 0,
+    FISH_ERR_ARG = 1,          /* invalid argument (sizes, keys, values, NULL) */
+    FISH_ERR_CUDA = 2,         /* CUDA runtime error (text in fish_last_error) */
+    FISH_ERR_OOM = 3,          /* device allocation failed */
+    FISH_ERR_STATE = 4,        /* call out of order (e.g. step before set_state) */
+    FISH_ERR_NONPHYSICAL = 5,  /* rho <= 0, p <= 0 or NaN met on the device */
+    FISH_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up */
+};
+
+enum { FISH_BC_PERIODIC = 0, FISH_BC_OUTFLOW = 1 };
+
+/* option keys for fish_set_option */
+enum {
+    FISH_OPT_PRECISION = 0,  /* FISH_PREC_FP64 (default) or FISH_PREC_FP32 */
+    FISH_OPT_LIMITER = 1,    /* FISH_LIM_VANLEER (default, eq0200), FISH_LIM_MINMOD (eq0190),
+                                FISH_LIM_NONE (first order, eq0140) */
+    FISH_OPT_HSE = 2,        /* 1: hydrostatic-gradient correction, eq0321-eq03261 */
+    FISH_OPT_PRED_DISS = 3,  /* predictor freezing-speed factor in [0,1] (Sec. 2.2); default 1 */
+    FISH_OPT_DX = 4,         /* cell widths; default 1/nx, 1/ny, 1/nz */
+    FISH_OPT_DY = 5,
+    FISH_OPT_DZ = 6
+};
+enum { FISH_PREC_FP64 = 0, FISH_PREC_FP32 = 1 };
+enum { FISH_LIM_VANLEER = 0, FISH_LIM_MINMOD = 1, FISH_LIM_NONE = 2 };
+
+/* dtype codes of device buffers */
+enum { FISH_F64 = 0, FISH_F32 = 1 };
+
+/* operators for fish_apply */
+enum { FISH_OP_FLUID = 0, FISH_OP_CT = 1 };
+
+/* Create a context for an nx*ny*nz box (each >= 1) with ratio of specific
+ * heats gamma > 1 and boundary condition bc.  No device memory is allocated
+ * until the first fish_set_state*.  *out receives the handle. */
+int fish_create(int nx, int ny, int nz, double gamma, int bc, fish_ctx **out);
+
+/* Set an option (keys above).  PRECISION may only change before the first
+ * fish_set_state*; the others may change between steps.  FISH_ERR_ARG for an
+ * unknown key or a value out of range. */
+int fish_set_option(fish_ctx *ctx, int key, double value);
+
+/* Queue all further work on this CUDA stream (a cudaStream_t, e.g. PyTorch's
+ * current stream); NULL selects the context's own non-blocking stream. */
+int fish_set_stream(fish_ctx *ctx, void *cuda_stream);
+
+/* Route the context's device allocations through a caller allocator (e.g.
+ * PyTorch's caching allocator): alloc(size, user) returns a device pointer or
+ * NULL, free(ptr, user) releases it.  Must be called before the first
+ * fish_set_state*.  NULL alloc restores cudaMalloc/cudaFree. */
+int fish_set_allocator(fish_ctx *ctx, void *(*alloc)(size_t size, void *user),
+                       void (*free_fn)(void *ptr, void *user), void *user);
+
+/* Upload the state from a host buffer of 8*nx*ny*nz doubles (layout above).
+ * Allocates device memory on first use.  Synchronous with respect to the
+ * host buffer (it may be reused on return). */
+int fish_set_state(fish_ctx *ctx, const double *state);
+
+/* Same from a device buffer of 8*nx*ny*nz values of dtype FISH_F64 or
+ * FISH_F32 (converted to the context precision).  Queued on the stream. */
+int fish_set_state_device(fish_ctx *ctx, const void *state, int dtype);
+
+/* Fixed cell-centred potential phi (nx*ny*nz doubles, host) for the unsplit
+ * gravity source (eq0253-eq0255); NULL removes gravity. */
+int fish_set_potential(fish_ctx *ctx, const double *phi);
+
+/* CFL time step dt = k * min over cells and axes d of h_d / (|v_d| + c_F,d)
+ * (eq0083-eq0084, reading C-15) for the current state.  Synchronises. */
+int fish_cfl_dt(fish_ctx *ctx, double k, double *dt_out);
+
+/* One full double step u^{n+2} = L_fwd L_bwd u^n (eq0081-eq0082, reading
+ * C-4): L_x B_x L_y B_y L_z B_z B_z L_z B_y L_y B_x L_x, every operator with
+ * the full dt, so time advances by 2*dt.  Asynchronous. */
+int fish_step(fish_ctx *ctx, double dt);
+
+/* nsteps double steps, each with dt = k * CFL of the state at its start,
+ * computed on the device (no host round trip); replayed as one CUDA graph
+ * per call after the first.  Asynchronous; fish_last_dt reads the last dt. */
+int fish_step_cfl(fish_ctx *ctx, double k, int nsteps);
+
+/* dt used by the last step of fish_step / fish_step_cfl.  Synchronises. */
+int fish_last_dt(fish_ctx *ctx, double *dt_out);
+
+/* Apply one operator -- FISH_OP_FLUID (L_dir) or FISH_OP_CT (B_dir) -- along
+ * axis dir (0 = x, 1 = y, 2 = z) with time step dt.  Asynchronous. */
+int fish_apply(fish_ctx *ctx, int op, int dir, double dt);
+
+/* Download the state to a host buffer of 8*nx*ny*nz doubles.  Synchronises. */
+int fish_get_state(fish_ctx *ctx, double *state);
+
+/* Copy the state into a device buffer of dtype FISH_F64 / FISH_F32.  Queued
+ * on the stream; returns pending device errors only after fish_sync. */
+int fish_get_state_device(fish_ctx *ctx, void *state, int dtype);
+
+/* out[0..7] = volume-weighted totals of the 8 fields (FP64 accumulation in a
+ * fixed order); out[8] = max |div b| (eq0341) over cells whose six faces are
+ * stored.  Synchronises. */
+int fish_diagnostics(fish_ctx *ctx, double out[9]);
+
+/* Wait for queued work; returns sticky device errors. */
+int fish_sync(fish_ctx *ctx);
+
+/* Clear the sticky device error flags (after the caller has handled them). */
+int fish_clear_error(fish_ctx *ctx);
+
+/* Text of the last error of this context (never NULL; "" if none). */
+const char *fish_last_error(fish_ctx *ctx);
+
+/* Number of kernel launches queued by this context since creation. */
+long long fish_launch_count(fish_ctx *ctx);
+
+/* Free all device memory and the handle.  NULL is ignored. */
+void fish_destroy(fish_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FISH_H */

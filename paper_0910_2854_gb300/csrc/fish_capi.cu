@@ -1,0 +1,630 @@
+// fish_capi.cu -- C ABI of libfish.so (declared in include/fish.h): context,
+// device memory, state transfer, the x-y-z-z-y-x double step (eq0081-eq0082,
+// reading C-4) and its CUDA-graph replay, CFL (eq0083-eq0084), diagnostics.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fish.h"
+#include "fish_launch.h"
+
+using fish::Geom;
+using fish::Launch;
+
+namespace {
+
+constexpr int kDiagBlocks = 1024;
+constexpr long long kStageChunk = 1ll << 25;  // doubles per conversion chunk (256 MB)
+
+}  // namespace
+
+struct fish_ctx {
+    int n[3] = {0, 0, 0};
+    long long N = 0;
+    double gamma = 0.0;
+    int bc = 0;
+    int prec = FISH_PREC_FP64;
+    int lim = FISH_LIM_VANLEER;
+    int hse = 0;
+    double alpha = 1.0;
+    double h[3] = {0, 0, 0};
+
+    cudaStream_t own = nullptr;
+    cudaStream_t stream = nullptr;
+    void *(*ualloc)(size_t, void *) = nullptr;
+    void (*ufree)(void *, void *) = nullptr;
+    void *uud = nullptr;
+    std::vector<void *> owned;
+
+    bool allocated = false;
+    void *fl[2][5] = {};   // fluid fields rho, m_x, m_y, m_z, E (two buffers)
+    void *bf[2][3] = {};   // face fields b_x, b_y, b_z (two buffers)
+    int cu = 0, cb = 0;    // current buffer of each group
+    void *phi = nullptr;
+    bool has_phi = false;
+
+    double *dt_dev = nullptr;       // time step read by the sweep kernels
+    double *dt_last = nullptr;      // dt of the last step
+    unsigned long long *minbits = nullptr;
+    unsigned *flags = nullptr;
+    double *partial = nullptr;
+    double *stage = nullptr;        // conversion staging (kStageChunk doubles)
+
+    cudaGraphExec_t gexec = nullptr;
+    double gk = -1.0;
+    int gparity = -1;
+    bool gdirty = true;
+
+    long long launches = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(fish_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+int cuda_fail(fish_ctx *c, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    (void)cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? FISH_ERR_OOM : FISH_ERR_CUDA, m);
+}
+
+#define FISH_CK(c, expr, what)                            \
+    do {                                                  \
+        cudaError_t e_ = (expr);                          \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+size_t esize(const fish_ctx *c) { return c->prec == FISH_PREC_FP64 ? sizeof(double) : sizeof(float); }
+
+void *dev_alloc(fish_ctx *c, size_t bytes)
+{
+    void *p = nullptr;
+    if (c->ualloc) {
+        p = c->ualloc(bytes, c->uud);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->owned.push_back(p);
+    return p;
+}
+
+void dev_free_all(fish_ctx *c)
+{
+    for (void *p : c->owned) {
+        if (c->ufree)
+            c->ufree(p, c->uud);
+        else
+            cudaFree(p);
+    }
+    c->owned.clear();
+}
+
+Geom geom(const fish_ctx *c)
+{
+    Geom g;
+    for (int a = 0; a < 3; ++a) g.n[a] = c->n[a];
+    g.st[0] = 1;
+    g.st[1] = c->n[0];
+    g.st[2] = (long long)c->n[0] * c->n[1];
+    g.bc = c->bc;
+    return g;
+}
+
+int ensure_alloc(fish_ctx *c)
+{
+    if (c->allocated) return FISH_OK;
+    const size_t bytes = (size_t)c->N * esize(c);
+    for (int b = 0; b < 2; ++b) {
+        for (int f = 0; f < 5; ++f)
+            if (!(c->fl[b][f] = dev_alloc(c, bytes))) return fail(c, FISH_ERR_OOM, "state allocation failed");
+        for (int f = 0; f < 3; ++f)
+            if (!(c->bf[b][f] = dev_alloc(c, bytes))) return fail(c, FISH_ERR_OOM, "state allocation failed");
+    }
+    c->dt_dev = (double *)dev_alloc(c, sizeof(double));
+    c->dt_last = (double *)dev_alloc(c, sizeof(double));
+    c->minbits = (unsigned long long *)dev_alloc(c, sizeof(unsigned long long));
+    c->flags = (unsigned *)dev_alloc(c, sizeof(unsigned));
+    c->partial = (double *)dev_alloc(c, sizeof(double) * 9 * kDiagBlocks);
+    if (!c->dt_dev || !c->dt_last || !c->minbits || !c->flags || !c->partial)
+        return fail(c, FISH_ERR_OOM, "scalar allocation failed");
+    const unsigned long long inf = 0x7FF0000000000000ull;
+    FISH_CK(c, cudaMemcpyAsync(c->minbits, &inf, sizeof(inf), cudaMemcpyHostToDevice, c->stream), "init");
+    FISH_CK(c, cudaMemsetAsync(c->flags, 0, sizeof(unsigned), c->stream), "init");
+    FISH_CK(c, cudaMemsetAsync(c->dt_dev, 0, sizeof(double), c->stream), "init");
+    FISH_CK(c, cudaMemsetAsync(c->dt_last, 0, sizeof(double), c->stream), "init");
+    FISH_CK(c, cudaStreamSynchronize(c->stream), "init");
+    c->allocated = true;
+    return FISH_OK;
+}
+
+int ensure_stage(fish_ctx *c)
+{
+    if (c->stage) return FISH_OK;
+    c->stage = (double *)dev_alloc(c, sizeof(double) * kStageChunk);
+    return c->stage ? FISH_OK : fail(c, FISH_ERR_OOM, "staging allocation failed");
+}
+
+void *field_ptr(fish_ctx *c, int f)
+{
+    return f < 5 ? c->fl[c->cu][f] : c->bf[c->cb][f - 5];
+}
+
+int check_flags(fish_ctx *c)
+{
+    unsigned fl = 0;
+    FISH_CK(c, cudaMemcpyAsync(&fl, c->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream), "flags");
+    FISH_CK(c, cudaStreamSynchronize(c->stream), "sync");
+    if (fl & fish::FLAG_TIMEOUT) return fail(c, FISH_ERR_TIMEOUT, "device wait timed out");
+    if (fl) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "non-physical state met on the device (flags 0x%x:%s%s%s)", fl,
+                 (fl & fish::FLAG_RHO) ? " rho<=0" : "", (fl & fish::FLAG_P) ? " p<=0" : "",
+                 (fl & fish::FLAG_NAN) ? " NaN" : "");
+        return fail(c, FISH_ERR_NONPHYSICAL, buf);
+    }
+    return FISH_OK;
+}
+
+// ---- operators -------------------------------------------------------------
+
+template <class T> int op_fluid(fish_ctx *c, int d)
+{
+    const T *in[8];
+    T *out[5];
+    for (int f = 0; f < 5; ++f) {
+        in[f] = (const T *)c->fl[c->cu][f];
+        out[f] = (T *)c->fl[1 - c->cu][f];
+    }
+    for (int f = 0; f < 3; ++f) in[5 + f] = (const T *)c->bf[c->cb][f];
+    FISH_CK(c,
+            Launch<T>::fluid(in, out, c->has_phi ? (const T *)c->phi : nullptr, c->dt_dev, geom(c), d, c->lim,
+                             c->hse != 0, c->gamma, c->alpha, c->h[d], c->flags, c->stream),
+            "fluid sweep launch");
+    c->cu = 1 - c->cu;
+    c->launches += 1;
+    return FISH_OK;
+}
+
+template <class T> int op_ct(fish_ctx *c, int d)
+{
+    const T *b[3];
+    T *bo[3];
+    for (int f = 0; f < 3; ++f) {
+        b[f] = (const T *)c->bf[c->cb][f];
+        bo[f] = (T *)c->bf[1 - c->cb][f];
+    }
+    FISH_CK(c,
+            Launch<T>::ct((const T *)c->fl[c->cu][0], (const T *)c->fl[c->cu][1 + d], b, bo, c->dt_dev, geom(c), d,
+                          c->lim, c->h, c->flags, c->stream),
+            "constrained-transport sweep launch");
+    c->cb = 1 - c->cb;
+    c->launches += 1;
+    return FISH_OK;
+}
+
+int apply_op(fish_ctx *c, int op, int d)
+{
+    if (c->prec == FISH_PREC_FP64)
+        return op == FISH_OP_FLUID ? op_fluid<double>(c, d) : op_ct<double>(c, d);
+    return op == FISH_OP_FLUID ? op_fluid<float>(c, d) : op_ct<float>(c, d);
+}
+
+// The twelve operators of one double step in time order (reading C-4).
+int queue_sweeps(fish_ctx *c)
+{
+    int r;
+    for (int d = 0; d < 3; ++d) {
+        if ((r = apply_op(c, FISH_OP_FLUID, d))) return r;
+        if ((r = apply_op(c, FISH_OP_CT, d))) return r;
+    }
+    for (int d = 2; d >= 0; --d) {
+        if ((r = apply_op(c, FISH_OP_CT, d))) return r;
+        if ((r = apply_op(c, FISH_OP_FLUID, d))) return r;
+    }
+    return FISH_OK;
+}
+
+template <class T> int queue_cfl(fish_ctx *c)
+{
+    const T *in[8];
+    for (int f = 0; f < 8; ++f) in[f] = (const T *)field_ptr(c, f);
+    FISH_CK(c, Launch<T>::cfl(in, geom(c), c->h, c->gamma, c->minbits, c->flags, c->stream), "cfl launch");
+    c->launches += 1;
+    return FISH_OK;
+}
+
+int queue_cfl_dt(fish_ctx *c, double k, double *dt_target, double *dt_copy)
+{
+    int r = c->prec == FISH_PREC_FP64 ? queue_cfl<double>(c) : queue_cfl<float>(c);
+    if (r) return r;
+    FISH_CK(c, fish::launch_cfl_finish(c->minbits, k, dt_target, dt_copy, c->stream), "cfl finish launch");
+    c->launches += 1;
+    return FISH_OK;
+}
+
+int ready(fish_ctx *c)
+{
+    if (!c) return FISH_ERR_ARG;
+    if (!c->allocated) return fail(c, FISH_ERR_STATE, "no state set (call fish_set_state first)");
+    return FISH_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int fish_create(int nx, int ny, int nz, double gamma, int bc, fish_ctx **out)
+{
+    if (!out) return FISH_ERR_ARG;
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || !(gamma > 1.0) || (bc != FISH_BC_PERIODIC && bc != FISH_BC_OUTFLOW))
+        return FISH_ERR_ARG;
+    if ((long long)nx * ny * nz > (1ll << 33)) return FISH_ERR_ARG;
+    fish_ctx *c = new (std::nothrow) fish_ctx;
+    if (!c) return FISH_ERR_OOM;
+    c->n[0] = nx;
+    c->n[1] = ny;
+    c->n[2] = nz;
+    c->N = (long long)nx * ny * nz;
+    c->gamma = gamma;
+    c->bc = bc;
+    c->h[0] = 1.0 / nx;
+    c->h[1] = 1.0 / ny;
+    c->h[2] = 1.0 / nz;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete c;
+        return FISH_ERR_CUDA;
+    }
+    c->stream = c->own;
+    *out = c;
+    return FISH_OK;
+}
+
+int fish_set_option(fish_ctx *c, int key, double v)
+{
+    if (!c) return FISH_ERR_ARG;
+    switch (key) {
+    case FISH_OPT_PRECISION:
+        if (v != FISH_PREC_FP64 && v != FISH_PREC_FP32) return fail(c, FISH_ERR_ARG, "bad precision");
+        if (c->allocated && (int)v != c->prec) return fail(c, FISH_ERR_STATE, "precision fixed after set_state");
+        c->prec = (int)v;
+        break;
+    case FISH_OPT_LIMITER:
+        if (v != 0 && v != 1 && v != 2) return fail(c, FISH_ERR_ARG, "bad limiter");
+        c->lim = (int)v;
+        break;
+    case FISH_OPT_HSE:
+        if (v != 0 && v != 1) return fail(c, FISH_ERR_ARG, "bad HSE switch");
+        c->hse = (int)v;
+        break;
+    case FISH_OPT_PRED_DISS:
+        if (!(v >= 0.0 && v <= 1.0)) return fail(c, FISH_ERR_ARG, "predictor factor outside [0,1]");
+        c->alpha = v;
+        break;
+    case FISH_OPT_DX:
+    case FISH_OPT_DY:
+    case FISH_OPT_DZ:
+        if (!(v > 0.0) || !std::isfinite(v)) return fail(c, FISH_ERR_ARG, "cell width must be > 0");
+        c->h[key - FISH_OPT_DX] = v;
+        break;
+    default:
+        return fail(c, FISH_ERR_ARG, "unknown option key");
+    }
+    c->gdirty = true;
+    return FISH_OK;
+}
+
+int fish_set_stream(fish_ctx *c, void *s)
+{
+    if (!c) return FISH_ERR_ARG;
+    c->stream = s ? (cudaStream_t)s : c->own;
+    c->gdirty = true;
+    return FISH_OK;
+}
+
+int fish_set_allocator(fish_ctx *c, void *(*alloc)(size_t, void *), void (*free_fn)(void *, void *), void *user)
+{
+    if (!c) return FISH_ERR_ARG;
+    if (c->allocated) return fail(c, FISH_ERR_STATE, "allocator must be set before set_state");
+    if (alloc && !free_fn) return fail(c, FISH_ERR_ARG, "allocator needs a free function");
+    c->ualloc = alloc;
+    c->ufree = alloc ? free_fn : nullptr;
+    c->uud = user;
+    return FISH_OK;
+}
+
+int fish_set_state(fish_ctx *c, const double *state)
+{
+    if (!c || !state) return FISH_ERR_ARG;
+    int r = ensure_alloc(c);
+    if (r) return r;
+    if (c->prec == FISH_PREC_FP64) {
+        for (int f = 0; f < 8; ++f)
+            FISH_CK(c, cudaMemcpyAsync(field_ptr(c, f), state + (long long)f * c->N, c->N * sizeof(double),
+                                       cudaMemcpyHostToDevice, c->stream),
+                    "state upload");
+    } else {
+        if ((r = ensure_stage(c))) return r;
+        for (int f = 0; f < 8; ++f)
+            for (long long o = 0; o < c->N; o += kStageChunk) {
+                const long long m = c->N - o < kStageChunk ? c->N - o : kStageChunk;
+                FISH_CK(c, cudaMemcpyAsync(c->stage, state + (long long)f * c->N + o, m * sizeof(double),
+                                           cudaMemcpyHostToDevice, c->stream),
+                        "state upload");
+                FISH_CK(c, Launch<float>::from_f64(c->stage, (float *)field_ptr(c, f) + o, m, c->stream), "convert");
+                c->launches += 1;
+            }
+    }
+    FISH_CK(c, cudaStreamSynchronize(c->stream), "state upload");
+    return FISH_OK;
+}
+
+int fish_set_state_device(fish_ctx *c, const void *state, int dtype)
+{
+    if (!c || !state || (dtype != FISH_F64 && dtype != FISH_F32)) return FISH_ERR_ARG;
+    int r = ensure_alloc(c);
+    if (r) return r;
+    for (int f = 0; f < 8; ++f) {
+        void *dst = field_ptr(c, f);
+        if (dtype == FISH_F64) {
+            const double *src = (const double *)state + (long long)f * c->N;
+            if (c->prec == FISH_PREC_FP64)
+                FISH_CK(c, cudaMemcpyAsync(dst, src, c->N * 8, cudaMemcpyDeviceToDevice, c->stream), "copy");
+            else
+                FISH_CK(c, Launch<float>::from_f64(src, (float *)dst, c->N, c->stream), "convert");
+        } else {
+            const float *src = (const float *)state + (long long)f * c->N;
+            if (c->prec == FISH_PREC_FP32)
+                FISH_CK(c, cudaMemcpyAsync(dst, src, c->N * 4, cudaMemcpyDeviceToDevice, c->stream), "copy");
+            else
+                FISH_CK(c, Launch<double>::from_f32(src, (double *)dst, c->N, c->stream), "convert");
+        }
+        c->launches += 1;
+    }
+    return FISH_OK;
+}
+
+int fish_set_potential(fish_ctx *c, const double *phi)
+{
+    if (!c) return FISH_ERR_ARG;
+    int r = ensure_alloc(c);
+    if (r) return r;
+    c->gdirty = true;
+    if (!phi) {
+        c->has_phi = false;
+        return FISH_OK;
+    }
+    if (!c->phi && !(c->phi = dev_alloc(c, (size_t)c->N * esize(c))))
+        return fail(c, FISH_ERR_OOM, "potential allocation failed");
+    if (c->prec == FISH_PREC_FP64) {
+        FISH_CK(c, cudaMemcpyAsync(c->phi, phi, c->N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "phi");
+    } else {
+        if ((r = ensure_stage(c))) return r;
+        for (long long o = 0; o < c->N; o += kStageChunk) {
+            const long long m = c->N - o < kStageChunk ? c->N - o : kStageChunk;
+            FISH_CK(c, cudaMemcpyAsync(c->stage, phi + o, m * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+                    "phi");
+            FISH_CK(c, Launch<float>::from_f64(c->stage, (float *)c->phi + o, m, c->stream), "convert");
+            c->launches += 1;
+        }
+    }
+    FISH_CK(c, cudaStreamSynchronize(c->stream), "phi upload");
+    c->has_phi = true;
+    return FISH_OK;
+}
+
+int fish_cfl_dt(fish_ctx *c, double k, double *dt_out)
+{
+    int r = ready(c);
+    if (r) return r;
+    if (!dt_out || !(k > 0.0)) return fail(c, FISH_ERR_ARG, "bad CFL arguments");
+    if ((r = queue_cfl_dt(c, k, c->partial, nullptr))) return r;
+    FISH_CK(c, cudaMemcpyAsync(dt_out, c->partial, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "dt");
+    return check_flags(c);
+}
+
+int fish_step(fish_ctx *c, double dt)
+{
+    int r = ready(c);
+    if (r) return r;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, FISH_ERR_ARG, "dt must be > 0");
+    FISH_CK(c, fish::launch_set_scalar(c->dt_dev, dt, c->stream), "dt");
+    FISH_CK(c, fish::launch_set_scalar(c->dt_last, dt, c->stream), "dt");
+    c->launches += 2;
+    return queue_sweeps(c);
+}
+
+int fish_step_cfl(fish_ctx *c, double k, int nsteps)
+{
+    int r = ready(c);
+    if (r) return r;
+    if (!(k > 0.0) || nsteps < 0) return fail(c, FISH_ERR_ARG, "bad arguments");
+    const int parity = c->cu * 2 + c->cb;
+    if (c->gdirty || !c->gexec || c->gk != k || c->gparity != parity) {
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        // capture one double step on a capturable stream
+        cudaStream_t cap = c->stream;
+        cudaGraph_t graph = nullptr;
+        const long long l0 = c->launches;
+        FISH_CK(c, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+        r = queue_cfl_dt(c, k, c->dt_dev, c->dt_last);
+        if (!r) r = queue_sweeps(c);
+        cudaError_t e = cudaStreamEndCapture(cap, &graph);
+        if (r) {
+            if (graph) cudaGraphDestroy(graph);
+            return r;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+        e = cudaGraphInstantiate(&c->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+        c->launches = l0;  // captured, not launched
+        c->gk = k;
+        c->gparity = parity;
+        c->gdirty = false;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        FISH_CK(c, cudaGraphLaunch(c->gexec, c->stream), "graph launch");
+        c->launches += 14;
+    }
+    return FISH_OK;
+}
+
+int fish_last_dt(fish_ctx *c, double *dt_out)
+{
+    int r = ready(c);
+    if (r) return r;
+    if (!dt_out) return FISH_ERR_ARG;
+    FISH_CK(c, cudaMemcpyAsync(dt_out, c->dt_last, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "dt");
+    return check_flags(c);
+}
+
+int fish_apply(fish_ctx *c, int op, int dir, double dt)
+{
+    int r = ready(c);
+    if (r) return r;
+    if ((op != FISH_OP_FLUID && op != FISH_OP_CT) || dir < 0 || dir > 2 || !(dt > 0.0))
+        return fail(c, FISH_ERR_ARG, "bad operator arguments");
+    FISH_CK(c, fish::launch_set_scalar(c->dt_dev, dt, c->stream), "dt");
+    c->launches += 1;
+    return apply_op(c, op, dir);
+}
+
+int fish_get_state(fish_ctx *c, double *state)
+{
+    int r = ready(c);
+    if (r) return r;
+    if (!state) return FISH_ERR_ARG;
+    if (c->prec == FISH_PREC_FP64) {
+        for (int f = 0; f < 8; ++f)
+            FISH_CK(c, cudaMemcpyAsync(state + (long long)f * c->N, field_ptr(c, f), c->N * sizeof(double),
+                                       cudaMemcpyDeviceToHost, c->stream),
+                    "state download");
+    } else {
+        if ((r = ensure_stage(c))) return r;
+        for (int f = 0; f < 8; ++f)
+            for (long long o = 0; o < c->N; o += kStageChunk) {
+                const long long m = c->N - o < kStageChunk ? c->N - o : kStageChunk;
+                FISH_CK(c, Launch<float>::to_f64((const float *)field_ptr(c, f) + o, c->stage, m, c->stream),
+                        "convert");
+                c->launches += 1;
+                FISH_CK(c, cudaMemcpyAsync(state + (long long)f * c->N + o, c->stage, m * sizeof(double),
+                                           cudaMemcpyDeviceToHost, c->stream),
+                        "state download");
+            }
+    }
+    return check_flags(c);
+}
+
+int fish_get_state_device(fish_ctx *c, void *state, int dtype)
+{
+    int r = ready(c);
+    if (r) return r;
+    if (!state || (dtype != FISH_F64 && dtype != FISH_F32)) return FISH_ERR_ARG;
+    for (int f = 0; f < 8; ++f) {
+        const void *src = field_ptr(c, f);
+        if (dtype == FISH_F64) {
+            double *dst = (double *)state + (long long)f * c->N;
+            if (c->prec == FISH_PREC_FP64)
+                FISH_CK(c, cudaMemcpyAsync(dst, src, c->N * 8, cudaMemcpyDeviceToDevice, c->stream), "copy");
+            else
+                FISH_CK(c, Launch<float>::to_f64((const float *)src, dst, c->N, c->stream), "convert");
+        } else {
+            float *dst = (float *)state + (long long)f * c->N;
+            if (c->prec == FISH_PREC_FP32)
+                FISH_CK(c, cudaMemcpyAsync(dst, src, c->N * 4, cudaMemcpyDeviceToDevice, c->stream), "copy");
+            else
+                FISH_CK(c, Launch<double>::to_f32((const double *)src, dst, c->N, c->stream), "convert");
+        }
+        c->launches += 1;
+    }
+    return FISH_OK;
+}
+
+int fish_diagnostics(fish_ctx *c, double out[9])
+{
+    int r = ready(c);
+    if (r) return r;
+    if (!out) return FISH_ERR_ARG;
+    const Geom g = geom(c);
+    if (c->prec == FISH_PREC_FP64) {
+        const double *in[8];
+        for (int f = 0; f < 8; ++f) in[f] = (const double *)field_ptr(c, f);
+        FISH_CK(c, Launch<double>::diag(in, g, c->h, c->partial, kDiagBlocks, c->stream), "diag launch");
+    } else {
+        const float *in[8];
+        for (int f = 0; f < 8; ++f) in[f] = (const float *)field_ptr(c, f);
+        FISH_CK(c, Launch<float>::diag(in, g, c->h, c->partial, kDiagBlocks, c->stream), "diag launch");
+    }
+    c->launches += 1;
+    std::vector<double> part((size_t)9 * kDiagBlocks);
+    FISH_CK(c, cudaMemcpyAsync(part.data(), c->partial, part.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                               c->stream),
+            "diag download");
+    FISH_CK(c, cudaStreamSynchronize(c->stream), "diag");
+    const double vol = c->h[0] * c->h[1] * c->h[2];
+    for (int f = 0; f < 9; ++f) out[f] = 0.0;
+    for (int b = 0; b < kDiagBlocks; ++b) {
+        for (int f = 0; f < 8; ++f) out[f] += part[(size_t)b * 9 + f];
+        out[8] = std::fmax(out[8], part[(size_t)b * 9 + 8]);
+    }
+    for (int f = 0; f < 8; ++f) out[f] *= vol;
+    return check_flags(c);
+}
+
+int fish_sync(fish_ctx *c)
+{
+    if (!c) return FISH_ERR_ARG;
+    if (!c->allocated) {
+        FISH_CK(c, cudaStreamSynchronize(c->stream), "sync");
+        return FISH_OK;
+    }
+    return check_flags(c);
+}
+
+int fish_clear_error(fish_ctx *c)
+{
+    if (!c) return FISH_ERR_ARG;
+    c->err.clear();
+    if (c->allocated) {
+        FISH_CK(c, cudaMemsetAsync(c->flags, 0, sizeof(unsigned), c->stream), "clear");
+        FISH_CK(c, cudaStreamSynchronize(c->stream), "clear");
+    }
+    return FISH_OK;
+}
+
+const char *fish_last_error(fish_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+long long fish_launch_count(fish_ctx *c) { return c ? c->launches : -1; }
+
+void fish_destroy(fish_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    dev_free_all(c);
+    if (c->own) cudaStreamDestroy(c->own);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,23 @@
+// fish_f64.cu -- FP64 instantiation of the sweep kernels.  Compiled without
+// FMA contraction (-fmad=false) so that every operation rounds like a plain
+// IEEE double evaluation of the paper's formulas, in the order written.
+#include "fish_launch.cuh"
+
+namespace fish {
+template struct Launch<double>;
+}
+
+namespace fish {
+cudaError_t launch_cfl_finish(unsigned long long *minbits, double k, double *dt, double *dt_copy,
+                              cudaStream_t s)
+{
+    cfl_finish_kernel<<<1, 1, 0, s>>>(minbits, k, dt, dt_copy);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_scalar(double *p, double v, cudaStream_t s)
+{
+    set_scalar_kernel<<<1, 1, 0, s>>>(p, v);
+    return cudaGetLastError();
+}
+}  // namespace fish

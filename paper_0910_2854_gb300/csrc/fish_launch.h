@@ -1,0 +1,37 @@
+// fish_launch.h -- host-side launchers of the sweep kernels for one real type.
+// The definitions (and the kernel instantiations) live in fish_f64.cu and
+// fish_f32.cu so that each precision is compiled with its own flags.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fish_types.h"
+
+namespace fish {
+
+template <class T> struct Launch {
+    // L_d: in[8] current state, out[5] fluid fields of the other buffer.
+    static cudaError_t fluid(const T *const in[8], T *const out[5], const T *phi, const double *dt,
+                             const Geom &g, int d, int lim, bool hse, double gamma, double alpha,
+                             double h, unsigned *flags, cudaStream_t s);
+    // B_d: rho, m_d of the current state; b[3] current field, bout[3] other.
+    static cudaError_t ct(const T *rho, const T *md, const T *const b[3], T *const bout[3],
+                          const double *dt, const Geom &g, int d, int lim, const double h[3],
+                          unsigned *flags, cudaStream_t s);
+    // CFL minimum into *minbits (order-preserving bits of a positive double).
+    static cudaError_t cfl(const T *const in[8], const Geom &g, const double h[3], double gamma,
+                           unsigned long long *minbits, unsigned *flags, cudaStream_t s);
+    // Per-block FP64 partial totals and max |div b| into partial[nblocks][9].
+    static cudaError_t diag(const T *const in[8], const Geom &g, const double h[3], double *partial,
+                            int nblocks, cudaStream_t s);
+    static cudaError_t from_f64(const double *src, T *dst, long long n, cudaStream_t s);
+    static cudaError_t from_f32(const float *src, T *dst, long long n, cudaStream_t s);
+    static cudaError_t to_f64(const T *src, double *dst, long long n, cudaStream_t s);
+    static cudaError_t to_f32(const T *src, float *dst, long long n, cudaStream_t s);
+};
+
+cudaError_t launch_cfl_finish(unsigned long long *minbits, double k, double *dt, double *dt_copy,
+                              cudaStream_t s);
+cudaError_t launch_set_scalar(double *p, double v, cudaStream_t s);
+
+}  // namespace fish

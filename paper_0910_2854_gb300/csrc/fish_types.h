@@ -1,0 +1,19 @@
+// fish_types.h -- host/device shared plain types of the sweep kernels.
+#pragma once
+
+namespace fish {
+
+// sticky device status bits (reading C-16: no floor, report instead)
+enum : unsigned { FLAG_RHO = 1u, FLAG_P = 2u, FLAG_NAN = 4u, FLAG_TIMEOUT = 8u };
+enum : int { LIM_VANLEER = 0, LIM_MINMOD = 1, LIM_NONE = 2 };
+enum : int { BC_PERIODIC = 0, BC_OUTFLOW = 1 };
+
+// Box geometry: cell counts, strides of the x-fastest layout (1, nx, nx*ny)
+// and boundary condition (0 periodic, 1 zeroth-order extrapolation).
+struct Geom {
+    int n[3];
+    long long st[3];
+    int bc;
+};
+
+}  // namespace fish
