@@ -1,0 +1,370 @@
+#!/usr/bin/env python
+"""Throughput of FISH's operator-split ideal-MHD double step on GB300.
+
+Metric: MHD cell-updates/s per full x-y-z-z-y-x double step (cells / step
+time, the step including the device CFL reduction), FP32 path on the
+1024^3 random-phase turbulence box, with the FP64 path on the 256^3
+Orszag-Tang box reported beside it, and the HBM roofline fraction of the
+dominant kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fish|reference]
+
+N > 1 runs as one rank per GPU under torch.distributed.run; every rank
+advances its own box (independent replicas, no collective on the data
+path), so scaling is weak and the value is the cells of all ranks divided by
+the slowest rank's time.  ``--impl reference`` times the CPU oracle (the
+FP64 C implementation in oracle/) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MHD cell-updates/s per full xyzzyx step"
+UNIT = "cell-updates/s"
+CFL = 0.5
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOAD = {
+    "workload": "random-phase MHD turbulence 1024^3 periodic, FP32 bulk with compensated pressure "
+                "recovery and FP64 reductions (k^-2 spectrum, |k|<=8, rms Mach 1, beta 1, rho=1, p=1, "
+                "seeds 910285/910286)",
+    "n": 1024,
+    "precision": "fp32",
+    "gamma": 5.0 / 3.0,
+}
+FP64_WORKLOAD = {
+    "workload": "3D Orszag-Tang-type vortex 256^3 periodic, FP64 (plain method)",
+    "n": 256,
+    "precision": "fp64",
+}
+# algorithmic bytes per cell of one launch (state fields the operator must
+# read and write, one word each): L_d reads 8 fields and writes 5, B_d reads
+# rho, m_d and 3 field components and writes 3.
+ALG_WORDS = {"fluid": 13, "ct": 8}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="fish", choices=("fish", "reference"))
+    p.add_argument("--n", type=int, default=None, help="override the box size (testing)")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.split(",") for r in self.tmp.read().strip().splitlines() if r.count(",") >= 8]
+        try:
+            os.unlink(self.tmp.name)
+        except OSError:
+            pass
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = [nm for i, nm in enumerate(names) if any(r[5 + i].strip() == "Active" for r in rows)]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_rate(n_twin=128, budget_s=10.0, min_steps=1, max_steps=50):
+    """Oracle cell-updates/s on the 128^3 twin of the turbulence box: whole
+    double steps (CFL included) until ``budget_s`` of CPU time."""
+    import oracle
+    from paper_0910_2854_gb300 import workloads as W
+    oracle.build()
+    w = W.turbulence(n_twin)
+    ob = oracle.OracleBox(*w.dims, w.gamma, bc=w.bc, h=w.h)
+    ob.set_state(w.state)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < min_steps or (time.perf_counter() - t0 < budget_s and steps < max_steps):
+        ob.step(ob.cfl(CFL))
+        steps += 1
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return w.ncells * steps / el, steps, el, cores, w.ncells
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    sample = 128 if args.n is None else min(args.n, 128)
+    # warm-up steps (untimed), then K timed steps on the bounded sample
+    rate_w, _, _, _, _ = oracle_rate(sample, budget_s=0.0, min_steps=max(1, min(args.warmup, 2)), max_steps=2)
+    import oracle
+    from paper_0910_2854_gb300 import workloads as W
+    w = W.turbulence(sample)
+    ob = oracle.OracleBox(*w.dims, w.gamma, bc=w.bc, h=w.h)
+    ob.set_state(w.state)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ob.step(ob.cfl(CFL))
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    value = w.ncells * args.steps / el
+    cfg = {"workload": WORKLOAD["workload"], "sample": "%d^3 twin of the workload" % sample,
+           "precision": "fp64 (oracle)", "cfl": CFL}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": cfg, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d double steps of the %d^3 twin" % (args.steps, sample)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def make_box(F, W, spec, n, torch):
+    prec = spec["precision"]
+    dt_ = torch.float32 if prec == "fp32" else torch.float64
+    if spec is WORKLOAD:
+        w = W.turbulence(n, device="cuda", dtype=dt_)
+        st = w.state
+    else:
+        w = W.orszag_tang(n)
+        st = torch.as_tensor(w.state, device="cuda", dtype=dt_)
+    box = F.Box(n, n, n, w.gamma, precision=prec, h=w.h)
+    box.set_state(st)
+    del st, w
+    torch.cuda.empty_cache()
+    return box
+
+
+def time_steps(box, torch, steps, warmup):
+    box.step_cfl(CFL, warmup)
+    box.sync()
+    s = box.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = box.launch_count()
+    e0.record(s)
+    box.step_cfl(CFL, steps)
+    e1.record(s)
+    e1.synchronize()
+    box.sync()
+    return e0.elapsed_time(e1), box.launch_count() - l0
+
+
+def time_operators(F, box, torch, reps=3):
+    """Average duration of each operator kind (CUDA events on the library's
+    stream), with the dt of the current state."""
+    dt = box.cfl_dt(CFL)
+    s = box.stream
+    out = {}
+    for kind, op in (("fluid", F.FISH_OP_FLUID), ("ct", F.FISH_OP_CT)):
+        for d in range(3):
+            box.apply(op, d, dt)  # warm
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                box.apply(op, d, dt)
+            e1.record(s)
+            e1.synchronize()
+            out["%s_%s" % (kind, "xyz"[d])] = e0.elapsed_time(e1) / reps
+    box.sync()
+    return out
+
+
+def traffic_per_cell(kernel_key):
+    """DRAM bytes per cell of one launch from the committed ncu summary, if
+    taken on the current kernels (profiles/traffic.json), else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        return t.get(kernel_key)
+    except Exception:
+        return None
+
+
+def e2e_rate(F, box, torch, n, steps):
+    """End to end through the public API: every step uploads the state from
+    pinned host memory (FP32, the path's arithmetic type), advances one
+    double step and reads back the step's CFL time step (8 bytes)."""
+    N = n ** 3
+    host = torch.empty((8, n, n, n), dtype=torch.float32, pin_memory=True)
+    dev = torch.empty((8, n, n, n), dtype=torch.float32, device="cuda")
+    box.get_state_device(dev)
+    host.copy_(dev)
+    del dev
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        box.set_state_host(host)
+        box.step_cfl(CFL, 1)
+        box.last_dt()
+    el = time.perf_counter() - t0
+    del host
+    return N * steps / el, 32 * N, 8
+
+
+def run_fish(args, rank, world, local):
+    import torch
+    import paper_0910_2854_gb300 as F
+    from paper_0910_2854_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n = args.n or WORKLOAD["n"]
+    box = make_box(F, W, WORKLOAD, n, torch)
+    clocks = ClockSampler(local)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    clocks.start()
+    ms, launches = time_steps(box, torch, args.steps, args.warmup)
+    barrier()
+    clk = clocks.stop()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * n ** 3 / (ms_step * 1e-3)
+
+    result = None
+    if rank == 0:
+        ops = time_operators(F, box, torch)
+        key = max(ops, key=ops.get)
+        kind = key.split("_")[0]
+        esz = 4 if WORKLOAD["precision"] == "fp32" else 8
+        alg = ALG_WORDS[kind] * esz * n ** 3
+        peak, peak_kind = measured_peak()
+        achieved = alg / (ops[key] * 1e-3) / 1e9
+        tpc = traffic_per_cell(key)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None if tpc is None else tpc * n ** 3, "kernel": key,
+                "kernel_ms": ops[key], "peak_source": peak_kind,
+                "step_alg_GBs": 384 * n ** 3 / (ms_step * 1e-3) / 1e9,
+                "step_frac": 384 * n ** 3 / (ms_step * 1e-3) / 1e9 / peak,
+                "op_ms": ops}
+        e2e = None
+        if not args.no_e2e:
+            try:
+                ev, hb, db = e2e_rate(F, box, torch, n, max(2, min(args.steps, 5)))
+                e2e = {"value": ev, "unit": UNIT, "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db}
+            except Exception as exc:  # report, do not hide
+                e2e = {"value": None, "unit": UNIT, "error": repr(exc)[:200]}
+        box.close()
+        torch.cuda.empty_cache()
+        fp64 = None
+        if not args.no_fp64:
+            b64 = make_box(F, W, FP64_WORKLOAD, FP64_WORKLOAD["n"], torch)
+            ms64, _ = time_steps(b64, torch, max(3, min(args.steps, 10)), args.warmup)
+            k64 = max(3, min(args.steps, 10))
+            v64 = FP64_WORKLOAD["n"] ** 3 / (ms64 / k64 * 1e-3)
+            fp64 = {"workload": FP64_WORKLOAD["workload"], "value": v64, "unit": UNIT, "ms_per_step": ms64 / k64,
+                    "fp32_over_fp64": (value / world) / v64}
+            b64.close()
+        cpu = None
+        if not args.no_cpu_baseline:
+            rate, steps, el, cores, cells = oracle_rate(128, budget_s=10.0)
+            cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": "%d double steps (%.1f s) of the 128^3 twin (%d cells) of the workload"
+                             % (steps, el, cells)}
+        result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                  "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                  "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded, generated on the device)",
+                  "config": {"workload": WORKLOAD["workload"], "cells": n ** 3, "cfl": CFL,
+                             "parallelism": "replicas x%d (one box per GPU, no data-path collective)" % world,
+                             "l2": "inputs larger than L2 (34 GB state vs 129 MB L2)",
+                             "graph": "one CUDA graph per double step (CFL + 12 sweeps)"},
+                  "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                  "clocks": clk, "fp64_path": fp64}
+    else:
+        box.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_fish(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

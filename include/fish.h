@@ -103,6 +103,10 @@ int fish_set_state(fish_ctx *ctx, const double *state);
  * FISH_F32 (converted to the context precision).  Queued on the stream. */
 int fish_set_state_device(fish_ctx *ctx, const void *state, int dtype);
 
+/* Same from a host buffer of dtype FISH_F64 or FISH_F32 (pinned host memory
+ * gives full copy bandwidth).  Returns once the buffer has been read. */
+int fish_set_state_host(fish_ctx *ctx, const void *state, int dtype);
+
 /* Fixed cell-centred potential phi (nx*ny*nz doubles, host) for the unsplit
  * gravity source (eq0253-eq0255); NULL removes gravity. */
 int fish_set_potential(fish_ctx *ctx, const double *phi);

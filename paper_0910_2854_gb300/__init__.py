@@ -29,7 +29,7 @@ FISH_OP_FLUID, FISH_OP_CT = 0, 1
 
 # every symbol include/fish.h declares (checked by the CPU test suite)
 EXPORTS = ("fish_create", "fish_set_option", "fish_set_stream", "fish_set_allocator", "fish_set_state",
-           "fish_set_state_device", "fish_set_potential", "fish_cfl_dt", "fish_step", "fish_step_cfl",
+           "fish_set_state_device", "fish_set_state_host", "fish_set_potential", "fish_cfl_dt", "fish_step", "fish_step_cfl",
            "fish_last_dt", "fish_apply", "fish_get_state", "fish_get_state_device", "fish_diagnostics",
            "fish_sync", "fish_clear_error", "fish_last_error", "fish_launch_count", "fish_destroy")
 
@@ -65,6 +65,7 @@ def load(path: str = LIB_PATH):
             "fish_set_allocator": ([P, _ALLOC_T, _FREE_T, P], ctypes.c_int),
             "fish_set_state": ([P, D], ctypes.c_int),
             "fish_set_state_device": ([P, P, ctypes.c_int], ctypes.c_int),
+            "fish_set_state_host": ([P, P, ctypes.c_int], ctypes.c_int),
             "fish_set_potential": ([P, D], ctypes.c_int),
             "fish_cfl_dt": ([P, ctypes.c_double, D], ctypes.c_int),
             "fish_step": ([P, ctypes.c_double], ctypes.c_int),
@@ -197,6 +198,24 @@ class Box:
         if a.size != 8 * np.prod(self.n):
             raise ValueError("state has %d values, expected %d" % (a.size, 8 * np.prod(self.n)))
         self._check(self._lib.fish_set_state(self.ctx, _dptr(a)), "fish_set_state")
+
+    def set_state_host(self, state):
+        """Upload from a host buffer (numpy array or CPU torch tensor, ideally
+        pinned), float64 or float32, without conversion on the host."""
+        if hasattr(state, "data_ptr"):
+            import torch
+            if state.dtype not in (torch.float64, torch.float32) or not state.is_contiguous():
+                raise ValueError("host state must be a contiguous float64/float32 tensor")
+            ptr, dt, size = state.data_ptr(), (FISH_F64 if state.dtype == torch.float64 else FISH_F32), state.numel()
+        else:
+            a = np.ascontiguousarray(state)
+            if a.dtype not in (np.float64, np.float32):
+                a = a.astype(np.float64)
+            ptr, dt, size = a.ctypes.data, (FISH_F64 if a.dtype == np.float64 else FISH_F32), a.size
+            self._keep = a
+        if size != 8 * np.prod(self.n):
+            raise ValueError("state has %d values, expected %d" % (size, 8 * np.prod(self.n)))
+        self._check(self._lib.fish_set_state_host(self.ctx, ctypes.c_void_p(ptr), dt), "fish_set_state_host")
 
     def set_potential(self, phi):
         if phi is None:

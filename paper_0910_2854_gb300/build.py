@@ -21,7 +21,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
           "--expt-relaxed-constexpr", "-I", CSRC, "-I", os.path.join(os.path.dirname(HERE), "include")]
 UNITS = {
     "fish_f64.cu": ["-fmad=false"],
-    "fish_f32.cu": [],
+    "fish_f32.cu": ["-prec-sqrt=false", "-ftz=true"],
     "fish_capi.cu": [],
 }
 

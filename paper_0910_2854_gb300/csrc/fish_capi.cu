@@ -45,7 +45,9 @@ struct fish_ctx {
     void *fl[2][5] = {};   // fluid fields rho, m_x, m_y, m_z, E (two buffers)
     void *bf[2][3] = {};   // face fields b_x, b_y, b_z (two buffers)
     int cu = 0, cb = 0;    // current buffer of each group
-    void *phi = nullptr;
+    int layout = 0;        // 0: x fastest (y, z sweeps); 1: y fastest (x sweeps)
+    void *phi = nullptr;   // potential, x-fastest layout
+    void *phiT = nullptr;  // potential, y-fastest layout
     bool has_phi = false;
 
     double *dt_dev = nullptr;       // time step read by the sweep kernels
@@ -111,16 +113,28 @@ void dev_free_all(fish_ctx *c)
     c->owned.clear();
 }
 
-Geom geom(const fish_ctx *c)
+Geom geom_of(const fish_ctx *c, int layout)
 {
     Geom g;
     for (int a = 0; a < 3; ++a) g.n[a] = c->n[a];
-    g.st[0] = 1;
-    g.st[1] = c->n[0];
+    if (layout == 0) {
+        g.st[0] = 1;
+        g.st[1] = c->n[0];
+        g.ord[0] = 0;
+        g.ord[1] = 1;
+    } else {
+        g.st[0] = c->n[1];
+        g.st[1] = 1;
+        g.ord[0] = 1;
+        g.ord[1] = 0;
+    }
     g.st[2] = (long long)c->n[0] * c->n[1];
+    g.ord[2] = 2;
     g.bc = c->bc;
     return g;
 }
+
+Geom geom(const fish_ctx *c) { return geom_of(c, c->layout); }
 
 int ensure_alloc(fish_ctx *c)
 {
@@ -161,6 +175,40 @@ void *field_ptr(fish_ctx *c, int f)
     return f < 5 ? c->fl[c->cu][f] : c->bf[c->cb][f - 5];
 }
 
+// Move the state of the current buffers into the other buffers in the
+// other layout (the paper's data rotation, Sec. 3, as a transpose).
+template <class T> int transpose_state(fish_ctx *c)
+{
+    const T *src[8];
+    T *dst[8];
+    for (int f = 0; f < 5; ++f) {
+        src[f] = (const T *)c->fl[c->cu][f];
+        dst[f] = (T *)c->fl[1 - c->cu][f];
+    }
+    for (int f = 0; f < 3; ++f) {
+        src[5 + f] = (const T *)c->bf[c->cb][f];
+        dst[5 + f] = (T *)c->bf[1 - c->cb][f];
+    }
+    const int nr = c->layout == 0 ? c->n[0] : c->n[1];
+    const int nc = c->layout == 0 ? c->n[1] : c->n[0];
+    FISH_CK(c, Launch<T>::transpose(src, dst, 8, nr, nc, c->n[2], c->stream), "transpose launch");
+    c->cu = 1 - c->cu;
+    c->cb = 1 - c->cb;
+    c->layout = 1 - c->layout;
+    c->launches += 1;
+    return FISH_OK;
+}
+
+int set_layout(fish_ctx *c, int layout)
+{
+    if (c->layout == layout) return FISH_OK;
+    // a layout change is only needed when both sizes are > 1
+    return c->prec == FISH_PREC_FP64 ? transpose_state<double>(c) : transpose_state<float>(c);
+}
+
+// layout an operator along d reads coalesced: y fastest for x sweeps
+inline int layout_for(int d) { return d == 0 ? 1 : 0; }
+
 int check_flags(fish_ctx *c)
 {
     unsigned fl = 0;
@@ -189,7 +237,8 @@ template <class T> int op_fluid(fish_ctx *c, int d)
     }
     for (int f = 0; f < 3; ++f) in[5 + f] = (const T *)c->bf[c->cb][f];
     FISH_CK(c,
-            Launch<T>::fluid(in, out, c->has_phi ? (const T *)c->phi : nullptr, c->dt_dev, geom(c), d, c->lim,
+            Launch<T>::fluid(in, out, c->has_phi ? (const T *)(c->layout ? c->phiT : c->phi) : nullptr, c->dt_dev,
+                             geom(c), d, c->lim,
                              c->hse != 0, c->gamma, c->alpha, c->h[d], c->flags, c->stream),
             "fluid sweep launch");
     c->cu = 1 - c->cu;
@@ -216,6 +265,8 @@ template <class T> int op_ct(fish_ctx *c, int d)
 
 int apply_op(fish_ctx *c, int op, int d)
 {
+    int r = set_layout(c, layout_for(d));
+    if (r) return r;
     if (c->prec == FISH_PREC_FP64)
         return op == FISH_OP_FLUID ? op_fluid<double>(c, d) : op_ct<double>(c, d);
     return op == FISH_OP_FLUID ? op_fluid<float>(c, d) : op_ct<float>(c, d);
@@ -355,6 +406,7 @@ int fish_set_state(fish_ctx *c, const double *state)
     if (!c || !state) return FISH_ERR_ARG;
     int r = ensure_alloc(c);
     if (r) return r;
+    c->layout = 0;
     if (c->prec == FISH_PREC_FP64) {
         for (int f = 0; f < 8; ++f)
             FISH_CK(c, cudaMemcpyAsync(field_ptr(c, f), state + (long long)f * c->N, c->N * sizeof(double),
@@ -381,6 +433,7 @@ int fish_set_state_device(fish_ctx *c, const void *state, int dtype)
     if (!c || !state || (dtype != FISH_F64 && dtype != FISH_F32)) return FISH_ERR_ARG;
     int r = ensure_alloc(c);
     if (r) return r;
+    c->layout = 0;
     for (int f = 0; f < 8; ++f) {
         void *dst = field_ptr(c, f);
         if (dtype == FISH_F64) {
@@ -401,6 +454,35 @@ int fish_set_state_device(fish_ctx *c, const void *state, int dtype)
     return FISH_OK;
 }
 
+int fish_set_state_host(fish_ctx *c, const void *state, int dtype)
+{
+    if (!c || !state || (dtype != FISH_F64 && dtype != FISH_F32)) return FISH_ERR_ARG;
+    if (dtype == FISH_F64) return fish_set_state(c, (const double *)state);
+    int r = ensure_alloc(c);
+    if (r) return r;
+    c->layout = 0;
+    if (c->prec == FISH_PREC_FP32) {
+        for (int f = 0; f < 8; ++f)
+            FISH_CK(c, cudaMemcpyAsync(field_ptr(c, f), (const float *)state + (long long)f * c->N,
+                                       c->N * sizeof(float), cudaMemcpyHostToDevice, c->stream),
+                    "state upload");
+    } else {
+        if ((r = ensure_stage(c))) return r;
+        float *stage = (float *)c->stage;
+        for (int f = 0; f < 8; ++f)
+            for (long long o = 0; o < c->N; o += kStageChunk) {
+                const long long m = c->N - o < kStageChunk ? c->N - o : kStageChunk;
+                FISH_CK(c, cudaMemcpyAsync(stage, (const float *)state + (long long)f * c->N + o, m * sizeof(float),
+                                           cudaMemcpyHostToDevice, c->stream),
+                        "state upload");
+                FISH_CK(c, Launch<double>::from_f32(stage, (double *)field_ptr(c, f) + o, m, c->stream), "convert");
+                c->launches += 1;
+            }
+    }
+    FISH_CK(c, cudaStreamSynchronize(c->stream), "state upload");
+    return FISH_OK;
+}
+
 int fish_set_potential(fish_ctx *c, const double *phi)
 {
     if (!c) return FISH_ERR_ARG;
@@ -413,6 +495,8 @@ int fish_set_potential(fish_ctx *c, const double *phi)
     }
     if (!c->phi && !(c->phi = dev_alloc(c, (size_t)c->N * esize(c))))
         return fail(c, FISH_ERR_OOM, "potential allocation failed");
+    if (!c->phiT && !(c->phiT = dev_alloc(c, (size_t)c->N * esize(c))))
+        return fail(c, FISH_ERR_OOM, "potential allocation failed");
     if (c->prec == FISH_PREC_FP64) {
         FISH_CK(c, cudaMemcpyAsync(c->phi, phi, c->N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "phi");
     } else {
@@ -424,6 +508,20 @@ int fish_set_potential(fish_ctx *c, const double *phi)
             FISH_CK(c, Launch<float>::from_f64(c->stage, (float *)c->phi + o, m, c->stream), "convert");
             c->launches += 1;
         }
+    }
+    {
+        // the x sweeps read the potential in the y-fastest layout
+        const void *src[8] = {c->phi};
+        void *dst[8] = {c->phiT};
+        if (c->prec == FISH_PREC_FP64)
+            FISH_CK(c, Launch<double>::transpose((const double *const *)src, (double *const *)dst, 1, c->n[0], c->n[1],
+                                                 c->n[2], c->stream),
+                    "phi transpose");
+        else
+            FISH_CK(c, Launch<float>::transpose((const float *const *)src, (float *const *)dst, 1, c->n[0], c->n[1],
+                                                c->n[2], c->stream),
+                    "phi transpose");
+        c->launches += 1;
     }
     FISH_CK(c, cudaStreamSynchronize(c->stream), "phi upload");
     c->has_phi = true;
@@ -456,6 +554,8 @@ int fish_step_cfl(fish_ctx *c, double k, int nsteps)
     int r = ready(c);
     if (r) return r;
     if (!(k > 0.0) || nsteps < 0) return fail(c, FISH_ERR_ARG, "bad arguments");
+    // every replay starts (and ends) in the layout of the x sweeps
+    if ((r = set_layout(c, layout_for(0)))) return r;
     const int parity = c->cu * 2 + c->cb;
     if (c->gdirty || !c->gexec || c->gk != k || c->gparity != parity) {
         if (c->gexec) {
@@ -485,7 +585,7 @@ int fish_step_cfl(fish_ctx *c, double k, int nsteps)
     }
     for (int s = 0; s < nsteps; ++s) {
         FISH_CK(c, cudaGraphLaunch(c->gexec, c->stream), "graph launch");
-        c->launches += 14;
+        c->launches += 16;
     }
     return FISH_OK;
 }
@@ -515,6 +615,7 @@ int fish_get_state(fish_ctx *c, double *state)
     int r = ready(c);
     if (r) return r;
     if (!state) return FISH_ERR_ARG;
+    if ((r = set_layout(c, 0))) return r;
     if (c->prec == FISH_PREC_FP64) {
         for (int f = 0; f < 8; ++f)
             FISH_CK(c, cudaMemcpyAsync(state + (long long)f * c->N, field_ptr(c, f), c->N * sizeof(double),
@@ -541,6 +642,7 @@ int fish_get_state_device(fish_ctx *c, void *state, int dtype)
     int r = ready(c);
     if (r) return r;
     if (!state || (dtype != FISH_F64 && dtype != FISH_F32)) return FISH_ERR_ARG;
+    if ((r = set_layout(c, 0))) return r;
     for (int f = 0; f < 8; ++f) {
         const void *src = field_ptr(c, f);
         if (dtype == FISH_F64) {

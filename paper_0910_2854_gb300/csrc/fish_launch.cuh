@@ -32,10 +32,13 @@ cudaError_t Launch<T>::fluid(const T *const in[8], T *const out[5], const T *phi
     A.h = h;
     A.flags = flags;
     const long long cols = (long long)g.n[(d + 1) % 3] * g.n[(d + 2) % 3];
+    const unsigned grid = grid_for(cols, 128);
     if (hse)
-        fluid_sweep_kernel<T, true><<<grid_for(cols, 128), 128, 0, s>>>(A);
+        fluid_sweep_kernel<T, true, true><<<grid, 128, 0, s>>>(A);   // HSE needs the potential
+    else if (phi)
+        fluid_sweep_kernel<T, false, true><<<grid, 128, 0, s>>>(A);
     else
-        fluid_sweep_kernel<T, false><<<grid_for(cols, 128), 128, 0, s>>>(A);
+        fluid_sweep_kernel<T, false, false><<<grid, 128, 0, s>>>(A);
     return cudaGetLastError();
 }
 
@@ -91,6 +94,24 @@ cudaError_t Launch<T>::diag(const T *const in[8], const Geom &g, const double h[
     for (int f = 0; f < 3; ++f) A.h[f] = h[f];
     A.partial = partial;
     diag_kernel<T><<<nblocks, 256, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t Launch<T>::transpose(const T *const src[8], T *const dst[8], int nf, int nr, int nc, int nz,
+                                 cudaStream_t s)
+{
+    TransArgs<T> A;
+    for (int f = 0; f < 8; ++f) {
+        A.src[f] = f < nf ? src[f] : nullptr;
+        A.dst[f] = f < nf ? dst[f] : nullptr;
+    }
+    A.nf = nf;
+    A.nr = nr;
+    A.nc = nc;
+    A.plane = (long long)nr * nc;
+    dim3 grid((nr + 31) / 32, (nc + 31) / 32, nz);
+    transpose_kernel<T><<<grid, dim3(32, 8), 0, s>>>(A);
     return cudaGetLastError();
 }
 

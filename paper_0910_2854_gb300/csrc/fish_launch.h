@@ -24,6 +24,9 @@ template <class T> struct Launch {
     // Per-block FP64 partial totals and max |div b| into partial[nblocks][9].
     static cudaError_t diag(const T *const in[8], const Geom &g, const double h[3], double *partial,
                             int nblocks, cudaStream_t s);
+    // per z-plane transpose of the 8 fields: nc rows of nr -> nr rows of nc
+    static cudaError_t transpose(const T *const src[8], T *const dst[8], int nf, int nr, int nc, int nz,
+                                 cudaStream_t s);
     static cudaError_t from_f64(const double *src, T *dst, long long n, cudaStream_t s);
     static cudaError_t from_f32(const float *src, T *dst, long long n, cudaStream_t s);
     static cudaError_t to_f64(const T *src, double *dst, long long n, cudaStream_t s);

@@ -36,6 +36,13 @@ template <> struct Real<float> {
     static __device__ __forceinline__ float min_(float a, float b) { return fminf(a, b); }
 };
 
+// Reciprocal and quotient: IEEE in FP64 (the oracle's rounding), the fast
+// hardware approximations (about 1-2 ulp) in FP32.
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double div_(double a, double b) { return a / b; }
+__device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
+
 // ---------------------------------------------------------------------------
 // limiters, eq0190 (minmod) and eq0200 (Van Leer); sign(0) = 0
 // ---------------------------------------------------------------------------
@@ -47,7 +54,7 @@ template <class T> __device__ __forceinline__ T sgn(T a)
 template <class T> __device__ __forceinline__ T limit(int lim, T a, T b)
 {
     if (lim == LIM_VANLEER) {
-        if (a * b > T(0)) return T(2) * a * b / (a + b);
+        if (a * b > T(0)) return div_(T(2) * a * b, a + b);
         return T(0);
     }
     if (lim == LIM_MINMOD)
@@ -98,16 +105,29 @@ __device__ __forceinline__ void cell_eval(const T u[5], const T bb[3], T gamma, 
     const T rho = u[0];
 #pragma unroll
     for (int k = 0; k < 5; ++k) c.u[k] = u[k];
-    const T v0 = u[1] / rho;
-    const T v1 = u[2] / rho;
-    const T v2 = u[3] / rho;
-    const T kin = T(0.5) * (u[1] * v0 + u[2] * v1 + u[3] * v2);
+    T v0, v1, v2, a2, bn2, bt2, p, kin;
     const T mag = T(0.5) * (bb[0] * bb[0] + bb[1] * bb[1] + bb[2] * bb[2]);
-    const T p = gas_pressure<T>(gm1, u[4], kin, mag);
+    if constexpr (sizeof(T) == 8) {
+        v0 = u[1] / rho;
+        v1 = u[2] / rho;
+        v2 = u[3] / rho;
+        kin = T(0.5) * (u[1] * v0 + u[2] * v1 + u[3] * v2);
+        p = gas_pressure<T>(gm1, u[4], kin, mag);
+        a2 = gamma * p / rho;
+        bn2 = bb[0] * bb[0] / rho;
+        bt2 = (bb[1] * bb[1] + bb[2] * bb[2]) / rho;
+    } else {
+        const T ri = rcp_(rho);
+        v0 = u[1] * ri;
+        v1 = u[2] * ri;
+        v2 = u[3] * ri;
+        kin = T(0.5) * (u[1] * v0 + u[2] * v1 + u[3] * v2);
+        p = gas_pressure<T>(gm1, u[4], kin, mag);
+        a2 = gamma * p * ri;
+        bn2 = bb[0] * bb[0] * ri;
+        bt2 = (bb[1] * bb[1] + bb[2] * bb[2]) * ri;
+    }
     const T ptot = p + mag;
-    const T a2 = gamma * p / rho;
-    const T bn2 = bb[0] * bb[0] / rho;
-    const T bt2 = (bb[1] * bb[1] + bb[2] * bb[2]) / rho;
     const T B2 = bn2 + bt2;
     // fast speed along the sweep; discriminant as a sum of squares
     const T disc = (a2 - B2) * (a2 - B2) + T(4) * a2 * bt2;
@@ -127,6 +147,41 @@ __device__ __forceinline__ void cell_eval(const T u[5], const T bb[3], T gamma, 
     if (rho != rho || p != p || c.cf != c.cf) flags |= FLAG_NAN;
 }
 
+// |v_n| + c_F along the frame's first axis only (CFL, eq0084); same
+// operations and order as cell_eval for those two quantities.
+template <class T>
+__device__ __forceinline__ T signal_speed(const T u[5], const T bb[3], T gamma, T gm1, unsigned &flags)
+{
+    const T rho = u[0];
+    T v0, a2, bn2, bt2, p, kin;
+    const T mag = T(0.5) * (bb[0] * bb[0] + bb[1] * bb[1] + bb[2] * bb[2]);
+    if constexpr (sizeof(T) == 8) {
+        v0 = u[1] / rho;
+        const T v1 = u[2] / rho, v2 = u[3] / rho;
+        kin = T(0.5) * (u[1] * v0 + u[2] * v1 + u[3] * v2);
+        p = gas_pressure<T>(gm1, u[4], kin, mag);
+        a2 = gamma * p / rho;
+        bn2 = bb[0] * bb[0] / rho;
+        bt2 = (bb[1] * bb[1] + bb[2] * bb[2]) / rho;
+    } else {
+        const T ri = rcp_(rho);
+        v0 = u[1] * ri;
+        const T v1 = u[2] * ri, v2 = u[3] * ri;
+        kin = T(0.5) * (u[1] * v0 + u[2] * v1 + u[3] * v2);
+        p = gas_pressure<T>(gm1, u[4], kin, mag);
+        a2 = gamma * p * ri;
+        bn2 = bb[0] * bb[0] * ri;
+        bt2 = (bb[1] * bb[1] + bb[2] * bb[2]) * ri;
+    }
+    const T B2 = bn2 + bt2;
+    const T disc = (a2 - B2) * (a2 - B2) + T(4) * a2 * bt2;
+    const T cf = Real<T>::sqrt_(T(0.5) * (a2 + B2 + Real<T>::sqrt_(disc)));
+    if (!(rho > T(0))) flags |= FLAG_RHO;
+    if (!(p > T(0))) flags |= FLAG_P;
+    if (rho != rho || p != p || cf != cf) flags |= FLAG_NAN;
+    return Real<T>::abs_(v0) + cf;
+}
+
 // hydrostatic estimate g (eq0321) and HSE-corrected difference (eq0323)
 template <class T>
 __device__ __forceinline__ void hse_delta(const Cell<T> &a, const Cell<T> &b, T phia, T phib, T du[5], T ddu[5])
@@ -136,7 +191,7 @@ __device__ __forceinline__ void hse_delta(const Cell<T> &a, const Cell<T> &b, T 
     xa[4] = -(a.u[4] + a.p);
     xb[0] = -b.u[0]; xb[1] = -b.u[1]; xb[2] = -b.u[2]; xb[3] = -b.u[3];
     xb[4] = -(b.u[4] + b.p);
-    const T fac = (phib - phia) / (a.cs * b.cs);
+    const T fac = div_(phib - phia, a.cs * b.cs);
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         const T gk = T(0.5) * (xb[k] + xa[k]) * fac;
@@ -172,7 +227,22 @@ template <class T, bool HSE>
 __device__ __forceinline__ void flux2(int lim, const Cell<T> &c0, const Cell<T> &c1, const Cell<T> &c2,
                                       const Cell<T> &c3, T ph0, T ph1, T ph2, T ph3, T F[5])
 {
-    if (!HSE) {
+    if (!HSE && sizeof(T) == 4) {
+        // FP32: the same flux written with differences of F and u, so each
+        // split-flux slope costs one multiply-add:
+        //   F+_{j+1} - F+_j = (dF_j + D du_j)/2,  F-_{j+1} - F-_j = (dF_j - D du_j)/2
+        //   F = (F_e + F_{e+1})/2 - D du_e/2 + [phi(+) - phi(-)]/2
+        const T D = Real<T>::max_(c1.d, c2.d);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const T df0 = c1.F[k] - c0.F[k], du0 = c1.u[k] - c0.u[k];
+            const T df1 = c2.F[k] - c1.F[k], du1 = c2.u[k] - c1.u[k];
+            const T df2 = c3.F[k] - c2.F[k], du2 = c3.u[k] - c2.u[k];
+            const T slp = limit(lim, df0 + D * du0, df1 + D * du1);
+            const T slm = limit(lim, df1 - D * du1, df2 - D * du2);
+            F[k] = T(0.5) * (c1.F[k] + c2.F[k]) - T(0.5) * D * du1 + T(0.25) * (slp - slm);
+        }
+    } else if (!HSE) {
         const T D = Real<T>::max_(c1.d, c2.d);
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
