@@ -156,6 +156,31 @@ const char *fish_last_error(fish_ctx *ctx);
 /* Number of kernel launches queued by this context since creation. */
 long long fish_launch_count(fish_ctx *ctx);
 
+/* Allocation-free diagnostics of a device-resident state.  The paper has no
+ * counterpart: this call serves callers that cannot let a library allocate
+ * device memory -- host codes that own all device memory through their own
+ * pool or budget, or time loops where a cudaMalloc (which may synchronise
+ * the device) is not allowed.  It needs no fish_ctx.
+ *   state : device buffer of 8*nx*ny*nz values of dtype FISH_F64/FISH_F32
+ *           in the state layout above (read only);
+ *   bc, dx, dy, dz : boundary condition and cell widths (> 0);
+ *   out   : DEVICE buffer of 9 doubles, written asynchronously on `stream`
+ *           (a cudaStream_t, NULL = legacy default stream): out[0..7] the
+ *           volume-weighted totals of the 8 fields, out[8] max |div b| over
+ *           cells whose six faces are stored -- the quantities of
+ *           fish_diagnostics, summed plane by plane in a fixed order.
+ * Scratch: a fixed device array of 4096 rows of 9 doubles (288 KiB) that
+ * every GPU loading the library keeps until exit; nz > 4096 is rejected
+ * with FISH_ERR_ARG.  All calls share it and each call rewrites the rows it
+ * uses, so calls whose kernels overlap on the GPU (unordered streams) race:
+ * order them.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Allocates nothing (no cudaMalloc, no
+ * allocator callback).  Returns FISH_ERR_ARG for bad arguments and
+ * FISH_ERR_CUDA if a launch fails. */
+int fish_diagnostics_noalloc(const void *state, int dtype, int nx, int ny, int nz, int bc, double dx,
+                             double dy, double dz, double *out, void *stream);
+
 /* Free all device memory and the handle.  NULL is ignored. */
 void fish_destroy(fish_ctx *ctx);
 

@@ -31,7 +31,8 @@ FISH_OP_FLUID, FISH_OP_CT = 0, 1
 EXPORTS = ("fish_create", "fish_set_option", "fish_set_stream", "fish_set_allocator", "fish_set_state",
            "fish_set_state_device", "fish_set_state_host", "fish_set_potential", "fish_cfl_dt", "fish_step", "fish_step_cfl",
            "fish_last_dt", "fish_apply", "fish_get_state", "fish_get_state_device", "fish_diagnostics",
-           "fish_sync", "fish_clear_error", "fish_last_error", "fish_launch_count", "fish_destroy")
+           "fish_sync", "fish_clear_error", "fish_last_error", "fish_launch_count", "fish_destroy",
+           "fish_diagnostics_noalloc")
 
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -80,6 +81,8 @@ def load(path: str = LIB_PATH):
             "fish_last_error": ([P], ctypes.c_char_p),
             "fish_launch_count": ([P], ctypes.c_longlong),
             "fish_destroy": ([P], None),
+            "fish_diagnostics_noalloc": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -282,3 +285,27 @@ class Box:
 
     def launch_count(self):
         return int(self._lib.fish_launch_count(self.ctx))
+
+
+def diagnostics_noalloc(state, dims, bc, h, out, stream=None):
+    """fish_diagnostics_noalloc: totals and max |div b| of the device state
+    tensor ``state`` (float64/float32, 8*nx*ny*nz values) into the device
+    tensor ``out`` (9 float64), queued on ``stream`` (a torch.cuda.Stream,
+    default: the current stream).  Allocates no device memory."""
+    import torch
+    lib = load()
+    if not (state.is_cuda and out.is_cuda and state.is_contiguous() and out.is_contiguous()):
+        raise ValueError("state and out must be contiguous CUDA tensors")
+    if state.dtype not in (torch.float64, torch.float32) or out.dtype != torch.float64 or out.numel() < 9:
+        raise ValueError("state must be float64/float32 and out 9 float64 values")
+    nx, ny, nz = (int(v) for v in dims)
+    if state.numel() != 8 * nx * ny * nz:
+        raise ValueError("state has the wrong size")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    code = lib.fish_diagnostics_noalloc(ctypes.c_void_p(state.data_ptr()),
+                                        FISH_F64 if state.dtype == torch.float64 else FISH_F32,
+                                        nx, ny, nz, int(bc), float(h[0]), float(h[1]), float(h[2]),
+                                        ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s.cuda_stream))
+    if code != FISH_OK:
+        raise FishError(code, "fish_diagnostics_noalloc failed")
+    return out

@@ -4,6 +4,7 @@ Three translation units compiled in parallel, then linked:
   fish_f64.cu  -- FP64 kernels, -fmad=false (IEEE rounding of each operation)
   fish_f32.cu  -- FP32 kernels (FMA contraction allowed)
   fish_capi.cu -- host-side C ABI
+  fish_noalloc.cu -- the allocation-free diagnostics entry point
 """
 from __future__ import annotations
 
@@ -23,6 +24,7 @@ UNITS = {
     "fish_f64.cu": ["-fmad=false"],
     "fish_f32.cu": ["-prec-sqrt=false", "-ftz=true"],
     "fish_capi.cu": [],
+    "fish_noalloc.cu": [],
 }
 
 
