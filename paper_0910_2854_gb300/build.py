@@ -3,6 +3,7 @@
 Three translation units compiled in parallel, then linked:
   fish_f64.cu  -- FP64 kernels, -fmad=false (IEEE rounding of each operation)
   fish_f32.cu  -- FP32 kernels (FMA contraction allowed)
+  fish_p2.cu   -- FP32 two-column sweep kernels (packed FP32x2)
   fish_capi.cu -- host-side C ABI
   fish_noalloc.cu -- the allocation-free diagnostics entry point
 """
@@ -23,6 +24,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
 UNITS = {
     "fish_f64.cu": ["-fmad=false"],
     "fish_f32.cu": ["-prec-sqrt=false", "-ftz=true"],
+    "fish_p2.cu": ["-prec-sqrt=false", "-ftz=true"],
     "fish_capi.cu": [],
     "fish_noalloc.cu": [],
 }
@@ -48,15 +50,19 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(s) <= t for s in sources())
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    if not force and up_to_date():
+def build(force: bool = False, verbose: bool = False, extra=(), lib=None) -> str:
+    """Compile the library (to ``lib``, default _build/libfish.so); ``extra``
+    nvcc flags are added to every unit (e.g. -D tuning macros)."""
+    out_lib = lib or LIB
+    if not force and lib is None and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     procs = []
     objs = []
+    tag = "" if lib is None else "_" + os.path.basename(out_lib).replace(".so", "")
     for unit, flags in UNITS.items():
-        obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, unit.replace(".cu", tag + ".o"))
         cmd = [cc, "-c", os.path.join(CSRC, unit), "-o", obj] + ARCH + COMMON + flags + list(extra)
         if verbose:
             print(" ".join(cmd))
@@ -71,11 +77,11 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             failed.append(unit)
     if failed:
         raise RuntimeError("nvcc failed for %s" % ", ".join(failed))
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = out_lib + ".%d.tmp" % os.getpid()
     cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, out_lib)
+    return out_lib
 
 
 if __name__ == "__main__":

@@ -1,0 +1,87 @@
+// fish_col_impl.cuh -- launchers of the column-march kernels for one
+// lane-vector type; included by the translation unit that instantiates them.
+#pragma once
+
+#include <type_traits>
+
+#include "fish_column.cuh"
+
+namespace fish {
+
+static inline unsigned col_grid(long long work, int block)
+{
+    long long g = (work + block - 1) / block;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+template <class V, bool HSE, bool GRAV, int LIM, bool FT1>
+static cudaError_t col_fluid_launch(const ColFluidArgs<typename VT<V>::S> &A, cudaStream_t s)
+{
+    const long long cols = (long long)(A.nf / VT<V>::W) * A.no;
+    fluid_col_kernel<V, HSE, GRAV, LIM, FT1><<<col_grid(cols, 128), 128, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <class V, bool HSE, bool GRAV, bool FT1>
+static cudaError_t col_fluid_lim(const ColFluidArgs<typename VT<V>::S> &A, cudaStream_t s)
+{
+    if constexpr (std::is_same<V, P2>::value) {
+        // compile-time limiters for the throughput path
+        if (A.lim == LIM_VANLEER) return col_fluid_launch<V, HSE, GRAV, LIM_VANLEER, FT1>(A, s);
+        if (A.lim == LIM_MINMOD) return col_fluid_launch<V, HSE, GRAV, LIM_MINMOD, FT1>(A, s);
+        return cudaErrorInvalidValue;
+    } else {
+        return col_fluid_launch<V, HSE, GRAV, -1, FT1>(A, s);
+    }
+}
+
+template <class V, bool FT1>
+static cudaError_t col_fluid_ft(const ColFluidArgs<typename VT<V>::S> &A, bool hse, cudaStream_t s)
+{
+    if constexpr (std::is_same<V, P2>::value) {
+        if (hse) return cudaErrorInvalidValue;  // the packed kernels carry no hydrostatic terms
+        if (A.phi) return col_fluid_lim<V, false, true, FT1>(A, s);
+        return col_fluid_lim<V, false, false, FT1>(A, s);
+    } else {
+        if (hse && A.phi) return col_fluid_lim<V, true, true, FT1>(A, s);
+        if (hse) return col_fluid_lim<V, true, false, FT1>(A, s);  // correction with phi = 0
+        if (A.phi) return col_fluid_lim<V, false, true, FT1>(A, s);
+        return col_fluid_lim<V, false, false, FT1>(A, s);
+    }
+}
+
+template <class V>
+cudaError_t col_fluid(const ColFluidArgs<typename VT<V>::S> &A, bool hse, bool ft1, cudaStream_t s)
+{
+    if constexpr (VT<V>::F64) {
+        return ft1 ? col_fluid_ft<V, true>(A, hse, s) : col_fluid_ft<V, false>(A, hse, s);
+    } else {
+        if (!ft1) return cudaErrorInvalidValue;
+        return col_fluid_ft<V, true>(A, hse, s);
+    }
+}
+
+template <class V, int LIM, bool FT1>
+static cudaError_t col_ct_launch(const ColCTArgs<typename VT<V>::S> &A, cudaStream_t s)
+{
+    // one warp per 31 W columns of a row (plus a halo lane)
+    const int segc = 31 * VT<V>::W;
+    const long long warps = (long long)((A.nf + segc - 1) / segc) * A.no;
+    ct_col_kernel<V, LIM, FT1><<<col_grid(warps * 32, 128), 128, 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <class V> cudaError_t col_ct(const ColCTArgs<typename VT<V>::S> &A, bool ft1, cudaStream_t s)
+{
+    if constexpr (VT<V>::F64) {
+        return ft1 ? col_ct_launch<V, -1, true>(A, s) : col_ct_launch<V, -1, false>(A, s);
+    } else if constexpr (std::is_same<V, P2>::value) {
+        if (A.lim == LIM_VANLEER) return col_ct_launch<V, LIM_VANLEER, true>(A, s);
+        if (A.lim == LIM_MINMOD) return col_ct_launch<V, LIM_MINMOD, true>(A, s);
+        return cudaErrorInvalidValue;
+    } else {
+        return col_ct_launch<V, -1, true>(A, s);
+    }
+}
+
+}  // namespace fish

@@ -1,0 +1,883 @@
+// fish_column.cuh -- column-march kernels of FISH's fluid operator L_d and
+// magnetic operator B_d (Kaeppeli et al., arXiv:0910.2854, Sec. 2-3).
+//
+// Geometry.  A sweep runs along axis d with element stride sd.  The two
+// transverse axes are the "fast" axis (element stride 1, the fastest memory
+// axis of the current layout) and the "other" axis (stride so).  A thread
+// owns W adjacent columns along the fast axis (V = P2: two FP32 columns
+// advanced together with packed FP32x2 arithmetic and 64-bit accesses;
+// V = float or double: one column) and marches them along d, so every global
+// access of a warp is coalesced.  In the x-fastest layout this serves the y
+// and z sweeps; the x sweeps run on the y-fastest copy of the state.
+//
+// The march is the paper's pipelined loop (Sec. 3) held in registers: raw
+// cell r enters, predicted cell r-1 is formed, corrected cell r-3 leaves.
+// Windows are indexed by r mod 4 (unrolled by four) so they rotate without
+// moves; the steady-state loop over interior cells carries no boundary tests,
+// ghost cells (periodic wrap or zeroth-order extrapolation, no ghost storage)
+// are handled by a short prologue and a guarded tail.
+//
+// Both operators read the current buffers and write the other ones.
+#pragma once
+
+#include "fish_math.cuh"
+#include "fish_types.h"
+#include "fish_vec.cuh"
+
+namespace fish {
+
+// ---------------------------------------------------------------------------
+// arguments
+// ---------------------------------------------------------------------------
+template <class S> struct ColFluidArgs {
+    const S *u[5];          // rho, m_d, m_t1, m_t2, E of the current buffer (sweep frame)
+    const S *bd, *bt1, *bt2;  // face fields b_d, b_t1, b_t2 (sweep frame)
+    S *uo[5];               // outputs, sweep frame
+    const S *phi;           // potential or nullptr
+    const double *dt;
+    long long sd, so;       // strides along the sweep and the other transverse axis
+    int n, nf, no;          // cells along the sweep, the fast and the other axis
+    int bc;
+    int lim;                // limiter (kernels with LIM < 0 read it at run time)
+    S gamma, gm1, alpha;
+    double h;               // cell width along d
+    unsigned *flags;
+};
+
+template <class S> struct ColCTArgs {
+    const S *rho, *md;      // density and momentum along d (unchanged by B_d)
+    const S *bd, *bf, *bo;  // b_d and the face fields of the fast and other transverse axes
+    S *bdo, *bfo, *boo;     // outputs (other buffer)
+    const double *dt;
+    long long sd, so;
+    int n, nf, no;
+    int bc;
+    int lim;
+    double h, hf, ho;       // cell widths along d, the fast and the other axis
+};
+
+// ---------------------------------------------------------------------------
+// per-cell arithmetic (frame: component 0 along d)
+// ---------------------------------------------------------------------------
+template <class V> struct CCell {
+    V u[5];
+    V F[5];
+    V d;                 // freezing speed |v_d| + c_F (label 0111)
+    V p, cs, cf, vn;     // used by the hydrostatic correction only
+};
+
+// running checks for reading C-16: min rho, min p, and a sum of c_F that
+// turns NaN if any evaluated cell produced one
+template <class V> struct Checks {
+    V mn_rho, mn_p, nsum;
+};
+
+template <class V> __device__ __forceinline__ void checks_init(Checks<V> &k)
+{
+    k.mn_rho = vb<V>(3.0e38f);
+    k.mn_p = vb<V>(3.0e38f);
+    k.nsum = vb<V>(0.0f);
+}
+
+template <class V> __device__ __forceinline__ unsigned checks_flags(const Checks<V> &k)
+{
+    unsigned f = 0;
+#pragma unroll
+    for (int i = 0; i < VT<V>::W; ++i) {
+        const auto r = vget(k.mn_rho, i), p = vget(k.mn_p, i), s = vget(k.nsum, i);
+        if (!(r > 0)) f |= FLAG_RHO;
+        if (!(p > 0)) f |= FLAG_P;
+        if (s != s) f |= FLAG_NAN;
+    }
+    return f;
+}
+
+// E - (kin + mag) with the rounding error of kin + mag carried by an
+// error-free two-sum (Knuth), so the cancellation against E costs no more
+// than the rounding of its inputs (the FP32 compensated island).
+__device__ __forceinline__ float eint_comp(float E, float kin, float mag)
+{
+    const float s = __fadd_rn(kin, mag);
+    const float bp = __fsub_rn(s, kin);
+    const float es = __fadd_rn(__fsub_rn(kin, __fsub_rn(s, bp)), __fsub_rn(mag, bp));
+    return __fsub_rn(__fsub_rn(E, s), es);
+}
+__device__ __forceinline__ P2 eint_comp(P2 E, P2 kin, P2 mag)
+{
+    const P2 s = kin + mag;
+    const P2 bp = s - kin;
+    const P2 es = (kin - (s - bp)) + (mag - bp);
+    return (E - s) - es;
+}
+
+// Primitives, flux vector (eq0100) and freezing speed (label 0111) of a cell
+// with conserved state u and cell-centred field bb (reading C-1 for c_F).
+template <class V>
+__device__ __forceinline__ void ceval(const V u[5], const V bb[3], V gamma, V gm1, CCell<V> &c, Checks<V> &k)
+{
+    const V rho = u[0];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) c.u[i] = u[i];
+    V v0, v1, v2, p, a2, bn2, bt2, mag;
+    if constexpr (VT<V>::F64) {
+        v0 = u[1] / rho;
+        v1 = u[2] / rho;
+        v2 = u[3] / rho;
+        const V kin = 0.5 * (u[1] * v0 + u[2] * v1 + u[3] * v2);
+        mag = 0.5 * (bb[0] * bb[0] + bb[1] * bb[1] + bb[2] * bb[2]);
+        p = gm1 * (u[4] - kin - mag);
+        a2 = gamma * p / rho;
+        bn2 = bb[0] * bb[0] / rho;
+        bt2 = (bb[1] * bb[1] + bb[2] * bb[2]) / rho;
+    } else {
+        const V half = vb<V>(0.5f);
+        const V ri = vrcp(rho);
+        v0 = u[1] * ri;
+        v1 = u[2] * ri;
+        v2 = u[3] * ri;
+        const V kin = half * vfma(u[3], v2, vfma(u[2], v1, u[1] * v0));
+        const V bb2 = bb[2] * bb[2];
+        const V bt = vfma(bb[1], bb[1], bb2);
+        const V bn = bb[0] * bb[0];
+        mag = half * (bn + bt);
+        p = gm1 * eint_comp(u[4], kin, mag);
+        a2 = gamma * p * ri;
+        bn2 = bn * ri;
+        bt2 = bt * ri;
+    }
+    const V ptot = p + mag;
+    const V B2 = bn2 + bt2;
+    V disc;
+    if constexpr (VT<V>::F64) disc = (a2 - B2) * (a2 - B2) + 4.0 * a2 * bt2;
+    else disc = vfma(a2 - B2, a2 - B2, vb<V>(4.0f) * a2 * bt2);
+    c.cf = vsqrt(vb<V>(0.5f) * (a2 + B2 + vsqrt(disc)));
+    c.cs = vsqrt(a2);
+    c.p = p;
+    c.vn = v0;
+    c.d = vabs(v0) + c.cf;
+    if constexpr (VT<V>::F64) {
+        const V bv = bb[0] * v0 + bb[1] * v1 + bb[2] * v2;
+        c.F[0] = u[1];
+        c.F[1] = u[1] * v0 + ptot - bb[0] * bb[0];
+        c.F[2] = u[2] * v0 - bb[0] * bb[1];
+        c.F[3] = u[3] * v0 - bb[0] * bb[2];
+        c.F[4] = (u[4] + ptot) * v0 - bb[0] * bv;
+    } else {
+        const V bv = vfma(bb[2], v2, vfma(bb[1], v1, bb[0] * v0));
+        const V nb0 = -bb[0];
+        c.F[0] = u[1];
+        c.F[1] = vfma(nb0, bb[0], vfma(u[1], v0, ptot));
+        c.F[2] = vfma(nb0, bb[1], u[2] * v0);
+        c.F[3] = vfma(nb0, bb[2], u[3] * v0);
+        c.F[4] = vfma(nb0, bv, (u[4] + ptot) * v0);
+    }
+    k.mn_rho = vmin(k.mn_rho, rho);
+    k.mn_p = vmin(k.mn_p, p);
+    k.nsum = k.nsum + c.cf;
+}
+
+// hydrostatic estimate g (eq0321) and the HSE-corrected difference (eq0323)
+template <class V>
+__device__ __forceinline__ void chse(const CCell<V> &a, const CCell<V> &b, V phia, V phib, V du[5], V ddu[5])
+{
+    V xa[5], xb[5];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        xa[i] = -a.u[i];
+        xb[i] = -b.u[i];
+    }
+    xa[4] = -(a.u[4] + a.p);
+    xb[4] = -(b.u[4] + b.p);
+    const V fac = vdiv(phib - phia, a.cs * b.cs);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const V g = vb<V>(0.5f) * (xb[i] + xa[i]) * fac;
+        du[i] = b.u[i] - a.u[i];
+        ddu[i] = vminmod(du[i] - g, du[i]);
+    }
+}
+
+// first-order interface flux: eq0140 with D = alpha max(d_a, d_b) (eq0150),
+// or the HSE-corrected form eq0324 (reading C-3)
+template <class V, bool HSE>
+__device__ __forceinline__ void cflux1(const CCell<V> &a, const CCell<V> &b, V phia, V phib, V alpha, V F[5])
+{
+    if constexpr (!HSE) {
+        const V D = alpha * vmax(a.d, b.d);
+        if constexpr (VT<V>::F64) {
+#pragma unroll
+            for (int i = 0; i < 5; ++i) F[i] = 0.5 * (a.F[i] + b.F[i]) - 0.5 * D * (b.u[i] - a.u[i]);
+        } else {
+            const V half = vb<V>(0.5f);
+#pragma unroll
+            for (int i = 0; i < 5; ++i) F[i] = half * vfma(-D, b.u[i] - a.u[i], a.F[i] + b.F[i]);
+        }
+    } else {
+        V du[5], ddu[5];
+        const V Dadv = alpha * vmax(vabs(a.vn), vabs(b.vn));
+        const V Dac = alpha * vmax(a.cf, b.cf);
+        chse(a, b, phia, phib, du, ddu);
+        const V half = vb<V>(0.5f);
+#pragma unroll
+        for (int i = 0; i < 5; ++i)
+            F[i] = half * (a.F[i] + b.F[i]) - half * Dadv * du[i] - half * Dac * ddu[i];
+    }
+}
+
+// second-order TVD flux at the interface c1|c2 from predicted cells c0..c3
+// (eq0160-eq0230; one freezing speed per interface, reading C-2; HSE form of
+// the slope differences, reading C-19)
+template <class V, bool HSE, int LIM>
+__device__ __forceinline__ void cflux2(const CCell<V> &c0, const CCell<V> &c1, const CCell<V> &c2, const CCell<V> &c3,
+                                       V ph0, V ph1, V ph2, V ph3, V F[5], int lim)
+{
+    if constexpr (!HSE && !VT<V>::F64) {
+        // FP32: F = (F_e + F_{e+1})/2 - D du_e/2 + [phi(+) - phi(-)]/4 with the
+        // split-flux slopes written as dF +- D du (each one multiply-add)
+        const V D = vmax(c1.d, c2.d);
+        const V nD = -D;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const V df0 = c1.F[i] - c0.F[i], du0 = c1.u[i] - c0.u[i];
+            const V df1 = c2.F[i] - c1.F[i], du1 = c2.u[i] - c1.u[i];
+            const V df2 = c3.F[i] - c2.F[i], du2 = c3.u[i] - c2.u[i];
+            const V slp = vlimit<LIM>(vfma(D, du0, df0), vfma(D, du1, df1), lim);
+            const V slm = vlimit<LIM>(vfma(nD, du1, df1), vfma(nD, du2, df2), lim);
+            F[i] = vfma(vb<V>(0.5f), vfma(nD, du1, c1.F[i] + c2.F[i]), vb<V>(0.25f) * (slp - slm));
+        }
+    } else if constexpr (!HSE) {
+        const V D = vmax(c1.d, c2.d);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const V fp0 = 0.5 * (c0.F[i] + D * c0.u[i]);
+            const V fp1 = 0.5 * (c1.F[i] + D * c1.u[i]);
+            const V fp2 = 0.5 * (c2.F[i] + D * c2.u[i]);
+            const V fm1 = 0.5 * (c1.F[i] - D * c1.u[i]);
+            const V fm2 = 0.5 * (c2.F[i] - D * c2.u[i]);
+            const V fm3 = 0.5 * (c3.F[i] - D * c3.u[i]);
+            const V slp = vlimit<LIM>(fp1 - fp0, fp2 - fp1, lim);
+            const V slm = vlimit<LIM>(fm2 - fm1, fm3 - fm2, lim);
+            F[i] = fp1 + fm2 + 0.5 * (slp - slm);
+        }
+    } else {
+        const V half = vb<V>(0.5f);
+        const V Dadv = vmax(vabs(c1.vn), vabs(c2.vn));
+        const V Dac = vmax(c1.cf, c2.cf);
+        V du0[5], dd0[5], du1[5], dd1[5], du2[5], dd2[5];
+        chse(c0, c1, ph0, ph1, du0, dd0);
+        chse(c1, c2, ph1, ph2, du1, dd1);
+        chse(c2, c3, ph2, ph3, du2, dd2);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const V q0 = Dadv * du0[i] + Dac * dd0[i];
+            const V q1 = Dadv * du1[i] + Dac * dd1[i];
+            const V q2 = Dadv * du2[i] + Dac * dd2[i];
+            const V fp_l = half * ((c1.F[i] - c0.F[i]) + q0);
+            const V fp_r = half * ((c2.F[i] - c1.F[i]) + q1);
+            const V fm_l = half * ((c2.F[i] - c1.F[i]) - q1);
+            const V fm_r = half * ((c3.F[i] - c2.F[i]) - q2);
+            const V slp = vlimit<LIM>(fp_l, fp_r, lim);
+            const V slm = vlimit<LIM>(fm_l, fm_r, lim);
+            F[i] = half * (c1.F[i] + c2.F[i]) - half * q1 + half * (slp - slm);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// L_d: fluid column march
+// ---------------------------------------------------------------------------
+template <class V> struct FRaw {
+    V u[5];
+    V bd;      // b_d at the cell's own (upper) face
+    V bdm;     // b_d at the lower face
+    V bf;      // fast-axis transverse face field at the cell's own faces
+    V bo, bom; // other-axis transverse face field at own / lower face
+    V phi;
+    typename VT<V>::S bfm;  // fast-axis field at the face below the first column
+};
+
+template <class V> struct FMarch {
+    FRaw<V> R;           // raw input of the next cell (prefetched)
+    CCell<V> C[2];       // evaluated raw cells r-1, r (slot r & 1)
+    V bb[2][3];          // their cell-centred field
+    V ph[2];             // their potential
+    V F1[2][5];          // predictor fluxes at (r-2, r-1), (r-1, r)
+    CCell<V> P[4];       // predicted cells (slot index mod 4)
+    V q[4];              // their potential
+    V F2[2][5];          // corrector fluxes
+    V phm2;              // potential of raw cell r-2
+    Checks<V> chk;
+};
+
+template <class S> struct FCtx {
+    long long base;      // offset of cell 0 of the first column
+    long long ofm;       // offset of the fast-axis face below the first column
+    long long oom;       // offset of the other-axis face below (mapped)
+};
+
+// load raw cell s (any s): every index through the boundary map; a ghost
+// cell copies the mapped cell as a whole, its lower b_d face included
+template <class V, bool GRAV, bool FT1>
+__device__ __forceinline__ void fload_mapped(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S> &X,
+                                             int s, FRaw<V> &R)
+{
+    const int cc = gmap(s, A.n, A.bc);
+    const long long i = X.base + (long long)cc * A.sd;
+    const long long im = X.base + (long long)gmap(cc - 1, A.n, A.bc) * A.sd;
+    const auto *bfp = FT1 ? A.bt1 : A.bt2;
+    const auto *bop = FT1 ? A.bt2 : A.bt1;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) R.u[k] = vload<V>(A.u[k], i);
+    R.bd = vload<V>(A.bd, i);
+    R.bdm = vload<V>(A.bd, im);
+    R.bf = vload<V>(bfp, i);
+    R.bfm = __ldg(bfp + i + X.ofm);
+    R.bo = vload<V>(bop, i);
+    R.bom = vload<V>(bop, i + X.oom);
+    if (GRAV) R.phi = vload<V>(A.phi, i);
+}
+
+// load interior cell at element offset i (no map; its lower b_d face is the
+// upper face of the previous cell, set by the caller)
+template <class V, bool GRAV, bool FT1>
+__device__ __forceinline__ void fload_direct(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S> &X,
+                                             long long i, FRaw<V> &R)
+{
+    const auto *bfp = FT1 ? A.bt1 : A.bt2;
+    const auto *bop = FT1 ? A.bt2 : A.bt1;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) R.u[k] = vload<V>(A.u[k], i);
+    R.bd = vload<V>(A.bd, i);
+    R.bf = vload<V>(bfp, i);
+    R.bfm = __ldg(bfp + i + X.ofm);
+    R.bo = vload<V>(bop, i);
+    R.bom = vload<V>(bop, i + X.oom);
+    if (GRAV) R.phi = vload<V>(A.phi, i);
+}
+
+// L2 prefetch distance of the steady-state loops (cells ahead of the load)
+#ifndef FISH_PF_DIST
+#define FISH_PF_DIST 2
+#endif
+
+// prefetch into L2 the fields the fluid march will load for interior cell i
+template <class V, bool GRAV, bool FT1>
+__device__ __forceinline__ void fprefetch(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S> &X,
+                                          long long i)
+{
+    const auto *bfp = FT1 ? A.bt1 : A.bt2;
+    const auto *bop = FT1 ? A.bt2 : A.bt1;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) pf_l2(A.u[k] + i);
+    pf_l2(A.bd + i);
+    pf_l2(bfp + i);
+    pf_l2(bop + i);
+    pf_l2(bop + i + X.oom);
+    if (GRAV) pf_l2(A.phi + i);
+}
+
+// Stage flags of one march step.
+enum : int { ST_F1 = 1, ST_PRED = 2, ST_F2 = 4, ST_OUT = 8 };
+// Load kinds: none, interior (direct), mapped.
+enum : int { LD_NONE = 0, LD_DIRECT = 1, LD_MAPPED = 2, LD_DIRECT_PF = 3 };
+
+// One step of the march for raw cell r (K = r mod 4).  The raw data of cell
+// r is in M.R on entry (loaded by the previous step); the step loads raw
+// cell r+1 (kind LD) into M.R.  FT1: the fast axis is t1 (else t2).
+template <class V, bool HSE, bool GRAV, int LIM, bool FT1, int K, int ST, int LD>
+__device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S> &X,
+                                      FMarch<V> &M, int r, V lam, V lamh, V hdt, V dt, V rtwoh)
+{
+    constexpr int k2 = K & 1, p2 = (K + 1) & 1;
+    const V half = vb<V>(0.5f);
+    // consume the raw input of cell r
+    V bbr[3];
+    V ur[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) ur[k] = M.R.u[k];
+    bbr[0] = half * (M.R.bdm + M.R.bd);
+    const V bd_r = M.R.bd;
+    const V bfc = half * (vshift_lo(M.R.bfm, M.R.bf) + M.R.bf);
+    const V boc = half * (M.R.bom + M.R.bo);
+    if constexpr (FT1) {
+        bbr[1] = bfc;
+        bbr[2] = boc;
+    } else {
+        bbr[1] = boc;
+        bbr[2] = bfc;
+    }
+    const V phr = GRAV ? M.R.phi : vb<V>(0.0f);  // no potential: phi = 0
+    // prefetch raw cell r+1
+    if constexpr (LD == LD_DIRECT || LD == LD_DIRECT_PF) {
+        fload_direct<V, GRAV, FT1>(A, X, X.base + (long long)(r + 1) * A.sd, M.R);
+        M.R.bdm = bd_r;
+        if constexpr (LD == LD_DIRECT_PF) {
+            const int pf = min(r + 1 + FISH_PF_DIST, A.n - 1);
+            fprefetch<V, GRAV, FT1>(A, X, X.base + (long long)pf * A.sd);
+        }
+    } else if constexpr (LD == LD_MAPPED) {
+        fload_mapped<V, GRAV, FT1>(A, X, r + 1, M.R);
+    }
+    // old state of the output cell o = r-3
+    const int o = r - 3;
+    const long long io = X.base + (long long)o * A.sd;
+    V un[5];
+    if constexpr ((ST & ST_OUT) != 0) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) un[k] = vload<V>(A.u[k], io);
+    }
+    ceval<V>(ur, bbr, vb<V>(A.gamma), vb<V>(A.gm1), M.C[k2], M.chk);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) M.bb[k2][k] = bbr[k];
+    if (GRAV || HSE) M.ph[k2] = phr;
+    if constexpr ((ST & ST_F1) != 0) {
+        // predictor flux at (r-1, r) (eq0140 / eq0324)
+        cflux1<V, HSE>(M.C[p2], M.C[k2], M.ph[p2], phr, vb<V>(A.alpha), M.F1[k2]);
+    }
+    if constexpr ((ST & ST_PRED) != 0) {
+        // predicted half step of cell r-1 (eq0253; source eq0254, reading C-6)
+        const CCell<V> &cp = M.C[p2];
+        V up[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            if constexpr (VT<V>::F64) up[k] = cp.u[k] - lamh * (M.F1[k2][k] - M.F1[p2][k]);
+            else up[k] = vfma(-lamh, M.F1[k2][k] - M.F1[p2][k], cp.u[k]);
+        }
+        if (GRAV) {
+            V dphi;
+            if constexpr (VT<V>::F64) dphi = (phr - M.phm2) / (2.0 * A.h);
+            else dphi = (phr - M.phm2) * rtwoh;
+            up[1] = up[1] - hdt * cp.u[0] * dphi;
+            up[4] = up[4] - hdt * cp.u[1] * dphi;
+        }
+        constexpr int s3 = (K + 3) & 3;  // slot of cell r-1
+        ceval<V>(up, M.bb[p2], vb<V>(A.gamma), vb<V>(A.gm1), M.P[s3], M.chk);
+        if (GRAV || HSE) M.q[s3] = M.ph[p2];
+        if constexpr ((ST & ST_F2) != 0) {
+            // corrector flux at (r-3, r-2) from predicted cells r-4 .. r-1 (eq0230)
+            constexpr int s0 = K & 3, s1 = (K + 1) & 3, s2 = (K + 2) & 3;
+            cflux2<V, HSE, LIM>(M.P[s0], M.P[s1], M.P[s2], M.P[s3], M.q[s0], M.q[s1], M.q[s2], M.q[s3], M.F2[k2],
+                                A.lim);
+            if constexpr ((ST & ST_OUT) != 0) {
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    if constexpr (VT<V>::F64) un[k] = un[k] - lam * (M.F2[k2][k] - M.F2[p2][k]);
+                    else un[k] = vfma(-lam, M.F2[k2][k] - M.F2[p2][k], un[k]);
+                }
+                if (GRAV) {
+                    // corrector source from the predicted state (eq0255)
+                    V dphi;
+                    if constexpr (VT<V>::F64) dphi = (M.q[s2] - M.q[s0]) / (2.0 * A.h);
+                    else dphi = (M.q[s2] - M.q[s0]) * rtwoh;
+                    un[1] = un[1] - dt * M.P[s1].u[0] * dphi;
+                    un[4] = un[4] - dt * M.P[s1].u[1] * dphi;
+                }
+#pragma unroll
+                for (int k = 0; k < 5; ++k) vstore(A.uo[k], io, un[k]);
+            }
+        }
+    }
+    if (GRAV) M.phm2 = M.ph[p2];
+}
+
+#ifndef FISH_COL_MINB
+#define FISH_COL_MINB 2
+#endif
+#ifndef FISH_COL_MINB1
+#define FISH_COL_MINB1 3   // one-column FP32 kernels
+#endif
+
+// L_d over all columns.  The prologue runs raw cells -3 .. 2 (K = 1, 2, 3,
+// 0, 1, 2); boxes with n < 8 load everything through the map.
+template <class V, bool HSE, bool GRAV, int LIM, bool FT1, int PLD>
+__device__ __forceinline__ void fprologue(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S> &X,
+                                          FMarch<V> &M, V lam, V lamh, V hdt, V dt, V rtwoh)
+{
+    fstep<V, HSE, GRAV, LIM, FT1, 1, 0, LD_MAPPED>(A, X, M, -3, lam, lamh, hdt, dt, rtwoh);
+    fstep<V, HSE, GRAV, LIM, FT1, 2, ST_F1, LD_MAPPED>(A, X, M, -2, lam, lamh, hdt, dt, rtwoh);
+    fstep<V, HSE, GRAV, LIM, FT1, 3, ST_F1 | ST_PRED, PLD>(A, X, M, -1, lam, lamh, hdt, dt, rtwoh);
+    fstep<V, HSE, GRAV, LIM, FT1, 0, ST_F1 | ST_PRED, PLD>(A, X, M, 0, lam, lamh, hdt, dt, rtwoh);
+    fstep<V, HSE, GRAV, LIM, FT1, 1, ST_F1 | ST_PRED, PLD>(A, X, M, 1, lam, lamh, hdt, dt, rtwoh);
+    fstep<V, HSE, GRAV, LIM, FT1, 2, ST_F1 | ST_PRED | ST_F2, PLD>(A, X, M, 2, lam, lamh, hdt, dt, rtwoh);
+}
+
+#ifndef FISH_COL_MINB
+#define FISH_COL_MINB 2
+#endif
+#ifndef FISH_COL_MINB1
+#define FISH_COL_MINB1 3   // one-column FP32 kernels
+#endif
+
+template <class V, bool HSE, bool GRAV, int LIM, bool FT1>
+__global__ void __launch_bounds__(128, VT<V>::F64 ? 1 : (VT<V>::W == 2 || HSE ? FISH_COL_MINB : FISH_COL_MINB1))
+    fluid_col_kernel(const ColFluidArgs<typename VT<V>::S> A)
+{
+    using S = typename VT<V>::S;
+    constexpr int W = VT<V>::W;
+    const int cols = A.nf / W;
+    const long long cid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cid >= (long long)cols * A.no) return;
+    const int fp = (int)(cid % cols), ob = (int)(cid / cols);
+    const int f0 = fp * W;
+    FCtx<S> X;
+    X.base = (long long)f0 + (long long)ob * A.so;
+    X.ofm = (long long)(gmap(f0 - 1, A.nf, A.bc) - f0);
+    X.oom = (long long)(gmap(ob - 1, A.no, A.bc) - ob) * A.so;
+    const double dtd = *A.dt;
+    const V dt = vb<V>(S(dtd));
+    const V lam = vb<V>(S(dtd / A.h));
+    const V lamh = vb<V>(S(dtd / (2.0 * A.h)));
+    const V hdt = vb<V>(S(0.5 * dtd));
+    const V rtwoh = vb<V>(S(1.0 / (2.0 * A.h)));
+    const int n = A.n;
+
+    FMarch<V> M;
+    checks_init(M.chk);
+    M.phm2 = vb<V>(0.0f);
+    M.ph[0] = M.ph[1] = vb<V>(0.0f);
+    fload_mapped<V, GRAV, FT1>(A, X, -3, M.R);
+    constexpr int ALL = ST_F1 | ST_PRED | ST_F2 | ST_OUT;
+    int r = 3;
+    if (n >= 8) {
+        fprologue<V, HSE, GRAV, LIM, FT1, LD_DIRECT>(A, X, M, lam, lamh, hdt, dt, rtwoh);
+        // steady state: the four steps r .. r+3 prefetch interior cells
+#pragma unroll 1
+        for (; r + 4 <= n - 1; r += 4) {
+            fstep<V, HSE, GRAV, LIM, FT1, 3, ALL, LD_DIRECT_PF>(A, X, M, r, lam, lamh, hdt, dt, rtwoh);
+            fstep<V, HSE, GRAV, LIM, FT1, 0, ALL, LD_DIRECT_PF>(A, X, M, r + 1, lam, lamh, hdt, dt, rtwoh);
+            fstep<V, HSE, GRAV, LIM, FT1, 1, ALL, LD_DIRECT_PF>(A, X, M, r + 2, lam, lamh, hdt, dt, rtwoh);
+            fstep<V, HSE, GRAV, LIM, FT1, 2, ALL, LD_DIRECT_PF>(A, X, M, r + 3, lam, lamh, hdt, dt, rtwoh);
+        }
+    } else {
+        fprologue<V, HSE, GRAV, LIM, FT1, LD_MAPPED>(A, X, M, lam, lamh, hdt, dt, rtwoh);
+    }
+    // tail: raw cells r .. n+2 (r = 3 mod 4, at most seven), loads through
+    // the map (harmless beyond n+2)
+    if (r <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, 3, ALL, LD_MAPPED>(A, X, M, r, lam, lamh, hdt, dt, rtwoh);
+    if (r + 1 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, 0, ALL, LD_MAPPED>(A, X, M, r + 1, lam, lamh, hdt, dt, rtwoh);
+    if (r + 2 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, 1, ALL, LD_MAPPED>(A, X, M, r + 2, lam, lamh, hdt, dt, rtwoh);
+    if (r + 3 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, 2, ALL, LD_MAPPED>(A, X, M, r + 3, lam, lamh, hdt, dt, rtwoh);
+    if (r + 4 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, 3, ALL, LD_MAPPED>(A, X, M, r + 4, lam, lamh, hdt, dt, rtwoh);
+    if (r + 5 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, 0, ALL, LD_MAPPED>(A, X, M, r + 5, lam, lamh, hdt, dt, rtwoh);
+    if (r + 6 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, 1, ALL, LD_NONE>(A, X, M, r + 6, lam, lamh, hdt, dt, rtwoh);
+    const unsigned fl = checks_flags(M.chk);
+    if (fl) atomicOr(A.flags, fl);
+}
+
+// ---------------------------------------------------------------------------
+// B_d: constrained transport column march (eq0330-eq0364, signs of C-5)
+// ---------------------------------------------------------------------------
+// Rolling state of one face pencil (windows indexed by cell s mod 4 or 2).
+template <class V> struct CFace {
+    V vt[4];   // face velocity (eq0361) at s
+    V vh[4];   // smoothed velocity (eq0362) at s-1
+    V bf[4];   // face field at s
+    V w[2];    // cell product v b at s-1
+    V f1[2];   // predictor flux at interface (s-2)'
+    V wp[4];   // predicted product at s-2
+    V f[2];    // corrector flux at interface (s-4)'
+};
+
+// Advance a face pencil by cell s (K = s mod 4) with face velocity vt and
+// field bf.  With OUT, bnew receives the updated face field of cell s-4 and
+// f[K & 1] holds the corrector flux at (s-4)'.
+template <class V, int LIM, int K, bool PRE1, bool PRE2, bool CORR, bool OUT>
+__device__ __forceinline__ void cface(CFace<V> &P, V vt, V bf, V lamh, V lam, V &bnew, int lim)
+{
+    constexpr int k1 = (K + 3) & 3, k2 = (K + 2) & 3, kp = (K + 1) & 3;
+    constexpr int e = K & 1, o = (K + 1) & 1;
+    // smoothed face velocity at s-1 (eq0362) and the cell product w_{s-1}
+    V vh;
+    if constexpr (VT<V>::F64) vh = 0.25 * (vt + 2.0 * P.vt[k1] + P.vt[k2]);
+    else vh = vb<V>(0.25f) * (vfma(vb<V>(2.0f), P.vt[k1], vt) + P.vt[k2]);
+    P.vh[k1] = vh;
+    P.w[o] = vh * P.bf[k1];
+    if constexpr (PRE1) {
+        // first-order upwind flux at (s-2)' (eq0363, edge velocity eq0364;
+        // tie v = 0 takes the right cell, reading C-7)
+        const V vbar = vb<V>(0.5f) * (P.vh[k2] + vh);
+        P.f1[e] = vsel_pos(vbar, P.w[e], P.w[o]);
+    }
+    if constexpr (PRE2) {
+        // predictor half step of the face field at s-2
+        V bp;
+        if constexpr (VT<V>::F64) bp = P.bf[k2] - lamh * (P.f1[e] - P.f1[o]);
+        else bp = vfma(-lamh, P.f1[e] - P.f1[o], P.bf[k2]);
+        P.wp[k2] = P.vh[k2] * bp;
+    }
+    if constexpr (CORR) {
+        // corrector flux at q' = (s-4)': piecewise-linear TVD about the
+        // upwind cell (reading C-10)
+        const V vbar = vb<V>(0.5f) * (P.vh[K] + P.vh[kp]);
+        const V wm = P.wp[k1], w0 = P.wp[K], w1 = P.wp[kp], w2 = P.wp[k2];
+        if constexpr (VT<V>::F64) {
+            P.f[e] = vbar > 0.0 ? w0 + 0.5 * vlimit<LIM>(w0 - wm, w1 - w0, lim) : w1 - 0.5 * vlimit<LIM>(w1 - w0, w2 - w1, lim);
+        } else {
+            // select the upwind operands, then limit once
+            const V d0 = w0 - wm, d1 = w1 - w0, d2 = w2 - w1;
+            const V la = vsel_pos(vbar, d0, d1);
+            const V lb = vsel_pos(vbar, d1, d2);
+            const V base = vsel_pos(vbar, w0, w1);
+            const V sg = vsel_pos(vbar, vb<V>(0.5f), vb<V>(-0.5f));
+            P.f[e] = vfma(sg, vlimit<LIM>(la, lb, lim), base);
+        }
+        if constexpr (OUT) {
+            if constexpr (VT<V>::F64) bnew = P.bf[K] - lam * (P.f[e] - P.f[o]);
+            else bnew = vfma(-lam, P.f[e] - P.f[o], P.bf[K]);
+        }
+    }
+    P.bf[K] = bf;
+    P.vt[K] = vt;
+}
+
+// ---------------------------------------------------------------------------
+// B_d column march.  A warp owns 31 W consecutive columns of one row of the
+// other axis (lanes 1..31) plus a halo lane 0 holding the W columns below:
+// every lane marches the face pencils above its columns along the fast axis
+// (PF) and along the other axis (PO), and the pencil below along the other
+// axis (PO-).  The fast-axis pencil below a column is the PF pencil of the
+// lane beneath it, whose edge flux arrives by a warp shuffle.  Raw inputs of
+// cell s+1 are loaded while cell s is computed.
+// ---------------------------------------------------------------------------
+template <class S> struct CTCtx {
+    long long base;      // element offset of the lane's first column in cell 0
+    long long ofp;       // offset to the fast-axis column above the lane's last column
+    long long oom, oop;  // offsets to the other-axis rows below / above (mapped)
+    bool active;         // lane stores its columns
+    bool fixy;           // halo lane at an outflow edge: its upper column is a copy of the lower
+};
+
+template <class V> struct CTRaw {
+    V rc, mc, ro, mo, rm, mm;   // rho, m_d of the lane's columns in this, the next and the previous row
+    typename VT<V>::S rf, mf;   // rho, m_d of the column above the lane's last column
+    V bF, bO, bOm;              // fast-axis faces; other-axis faces of this and the previous row
+    V bdo;                      // b_d of the output cell s-4
+};
+
+template <class V> __device__ __forceinline__ void fixy_(V &a, bool f)
+{
+    if constexpr (VT<V>::W == 2) {
+        if (f) a.v.y = a.v.x;
+    }
+}
+
+// load the raw inputs of cell s (MAPPED: s through the boundary map; OUTLD:
+// also b_d of the output cell s-4, which is interior)
+template <class V, bool MAPPED, bool OUTLD>
+__device__ __forceinline__ void ctload(const ColCTArgs<typename VT<V>::S> &A, const CTCtx<typename VT<V>::S> &X, int s,
+                                       CTRaw<V> &R)
+{
+    const long long i = X.base + (long long)(MAPPED ? gmap(s, A.n, A.bc) : s) * A.sd;
+    R.rc = vload<V>(A.rho, i);
+    R.mc = vload<V>(A.md, i);
+    R.ro = vload<V>(A.rho, i + X.oop);
+    R.mo = vload<V>(A.md, i + X.oop);
+    R.rm = vload<V>(A.rho, i + X.oom);
+    R.mm = vload<V>(A.md, i + X.oom);
+    R.rf = __ldg(A.rho + i + X.ofp);
+    R.mf = __ldg(A.md + i + X.ofp);
+    R.bF = vload<V>(A.bf, i);
+    R.bO = vload<V>(A.bo, i);
+    R.bOm = vload<V>(A.bo, i + X.oom);
+    if constexpr (VT<V>::W == 2) {
+        if (X.fixy) {
+            fixy_(R.rc, true); fixy_(R.mc, true); fixy_(R.ro, true); fixy_(R.mo, true);
+            fixy_(R.rm, true); fixy_(R.mm, true); fixy_(R.bF, true); fixy_(R.bO, true); fixy_(R.bOm, true);
+        }
+    }
+    // (the tail's last step loads one cell past the march: keep its index in range)
+    if constexpr (OUTLD) R.bdo = vload<V>(A.bd, X.base + (long long)(MAPPED ? min(s - 4, A.n - 1) : s - 4) * A.sd);
+}
+
+// prefetch into L2 the fields of interior cell i
+template <class V>
+__device__ __forceinline__ void ctprefetch(const ColCTArgs<typename VT<V>::S> &A, const CTCtx<typename VT<V>::S> &X,
+                                           long long i)
+{
+    pf_l2(A.rho + i);
+    pf_l2(A.md + i);
+    pf_l2(A.rho + i + X.oom);
+    pf_l2(A.md + i + X.oom);
+    pf_l2(A.rho + i + X.oop);
+    pf_l2(A.md + i + X.oop);
+    pf_l2(A.bf + i);
+    pf_l2(A.bo + i);
+    pf_l2(A.bo + i + X.oom);
+    pf_l2(A.bd + i);
+}
+
+template <class V> struct CTMarch {
+    CFace<V> PF, PO, POm;   // fast-axis faces above, other-axis faces above / below
+    CTRaw<V> R;             // raw inputs of the next cell
+};
+
+template <class V> __device__ __forceinline__ V shfl_up1(V a)
+{
+    if constexpr (VT<V>::W == 2) return {make_float2(__shfl_up_sync(0xffffffffu, a.v.x, 1),
+                                                     __shfl_up_sync(0xffffffffu, a.v.y, 1))};
+    else return __shfl_up_sync(0xffffffffu, a, 1);
+}
+
+// Load kinds of a CT step (for cell s+1): none, interior, interior with L2
+// prefetch, through the map.
+enum : int { CL_NONE = 0, CL_DIRECT = 1, CL_DIRECT_PF = 2, CL_MAPPED = 3 };
+
+// One cell s of the CT march (K = s mod 4); the raw inputs of s are in M.R.
+// Next loads cell s+1 (kind LD; NOUT: with b_d of cell s-3 for its output).
+template <class V, int LIM, bool FT1, int K, bool PRE1, bool PRE2, bool CORR, bool OUT, int LD, bool NOUT>
+__device__ __forceinline__ void ctstep(const ColCTArgs<typename VT<V>::S> &A, const CTCtx<typename VT<V>::S> &X,
+                                       CTMarch<V> &M, int s, V lamh, V lam, V lamf, V lamo)
+{
+    // consume the raw inputs of cell s
+    const V vc = vdiv(M.R.mc, M.R.rc);
+    const V vop = vdiv(M.R.mo, M.R.ro);
+    const V vom = vdiv(M.R.mm, M.R.rm);
+    V vfp;
+    if constexpr (VT<V>::W == 2) vfp = vshift_hi(vc, __fdividef(M.R.mf, M.R.rf));
+    else vfp = vdiv(V(M.R.mf), V(M.R.rf));
+    const V bF = M.R.bF, bO = M.R.bO, bOm = M.R.bOm;
+    const V bdo = M.R.bdo;
+    // load cell s+1
+    if constexpr (LD == CL_DIRECT || LD == CL_DIRECT_PF) {
+        ctload<V, false, NOUT>(A, X, s + 1, M.R);
+        if constexpr (LD == CL_DIRECT_PF)
+            ctprefetch<V>(A, X, X.base + (long long)min(s + 1 + FISH_PF_DIST, A.n - 1) * A.sd);
+    } else if constexpr (LD == CL_MAPPED) {
+        ctload<V, true, NOUT>(A, X, s + 1, M.R);
+    }
+    const V half = vb<V>(0.5f);
+    V nF, nO, dummy;
+    cface<V, LIM, K, PRE1, PRE2, CORR, OUT>(M.PF, half * (vc + vfp), bF, lamh, lam, nF, A.lim);
+    cface<V, LIM, K, PRE1, PRE2, CORR, OUT>(M.PO, half * (vc + vop), bO, lamh, lam, nO, A.lim);
+    cface<V, LIM, K, PRE1, PRE2, CORR, false>(M.POm, half * (vom + vc), bOm, lamh, lam, dummy, A.lim);
+    if constexpr (OUT) {
+        constexpr int e = K & 1;
+        // edge flux of the fast-axis face below: the upper pencil of the lane beneath
+        const V fup = M.PF.f[e];
+        const V sh = shfl_up1(fup);
+        V fdn;
+        if constexpr (VT<V>::W == 2) fdn = vshift_lo(sh.v.y, fup);
+        else fdn = sh;
+        if (X.active) {
+            const long long io = X.base + (long long)(s - 4) * A.sd;
+            vstore(A.bfo, io, nF);
+            vstore(A.boo, io, nO);
+            const V tF = fup - fdn, tO = M.PO.f[e] - M.POm.f[e];
+            V r;
+            if constexpr (VT<V>::F64) {
+                if constexpr (FT1) r = bdo + lamf * tF + lamo * tO;
+                else r = bdo + lamo * tO + lamf * tF;
+            } else {
+                r = vfma(lamo, tO, vfma(lamf, tF, bdo));
+            }
+            vstore(A.bdo, io, r);
+        }
+    }
+}
+
+#ifndef FISH_CT_MINB
+#define FISH_CT_MINB 3
+#endif
+
+// B_d over all columns (eq0350 advection of the transverse components,
+// eq0360 constraint update of b_d from the same edge fluxes).  Every lane of
+// a warp takes the same steps (shuffles); lanes without columns of their
+// own repeat a valid column and store nothing.
+template <class V, int LIM, bool FT1>
+__global__ void __launch_bounds__(128, VT<V>::F64 ? 1 : FISH_CT_MINB) ct_col_kernel(const ColCTArgs<typename VT<V>::S> A)
+{
+    using S = typename VT<V>::S;
+    constexpr int W = VT<V>::W;
+    constexpr int SEGC = 31 * W;  // output columns per warp
+    const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nseg = (A.nf + SEGC - 1) / SEGC;
+    if (gw >= (long long)nseg * A.no) return;  // whole warps only
+    const int seg = (int)(gw % nseg), ob = (int)(gw / nseg);
+    int cl = seg * SEGC + (lane - 1) * W;       // first logical column of the lane
+    CTCtx<S> X;
+    X.active = lane >= 1 && cl < A.nf;
+    if (lane >= 1 && cl >= A.nf) cl = A.nf - W;  // idle lane: repeat a valid column
+    int cb;                                      // physical first column
+    X.fixy = false;
+    if (cl >= 0) {
+        cb = cl;
+    } else if (A.bc == BC_PERIODIC) {
+        cb = cl + A.nf;
+    } else {
+        cb = 0;
+        X.fixy = W == 2;
+    }
+    const int cfp = gmap(cl + W, A.nf, A.bc);
+    X.base = (long long)cb + (long long)ob * A.so;
+    X.ofp = (long long)(cfp - cb);
+    X.oom = (long long)(gmap(ob - 1, A.no, A.bc) - ob) * A.so;
+    X.oop = (long long)(gmap(ob + 1, A.no, A.bc) - ob) * A.so;
+    const double dtd = *A.dt;
+    const V lamh = vb<V>(S(dtd / (2.0 * A.h)));
+    const V lam = vb<V>(S(dtd / A.h));
+    const V lamf = vb<V>(S(dtd / A.hf));
+    const V lamo = vb<V>(S(dtd / A.ho));
+    const int n = A.n;
+    CTMarch<V> M;
+    {
+        CFace<V> z;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) z.vt[k] = z.vh[k] = z.bf[k] = z.wp[k] = vb<V>(0.0f);
+        z.w[0] = z.w[1] = z.f1[0] = z.f1[1] = z.f[0] = z.f[1] = vb<V>(0.0f);
+        M.PF = M.PO = M.POm = z;
+    }
+    M.R.bdo = vb<V>(0.0f);
+    ctload<V, true, false>(A, X, -4, M.R);
+    // prologue s = -4 .. 3 (stages switch on at -1, 0, 3); cells 0 .. 3 are
+    // loaded directly when n >= 4
+    ctstep<V, LIM, FT1, 0, false, false, false, false, CL_MAPPED, false>(A, X, M, -4, lamh, lam, lamf, lamo);
+    ctstep<V, LIM, FT1, 1, false, false, false, false, CL_MAPPED, false>(A, X, M, -3, lamh, lam, lamf, lamo);
+    ctstep<V, LIM, FT1, 2, false, false, false, false, CL_MAPPED, false>(A, X, M, -2, lamh, lam, lamf, lamo);
+    int s = 4;
+    if (n >= 8) {
+        ctstep<V, LIM, FT1, 3, true, false, false, false, CL_DIRECT, false>(A, X, M, -1, lamh, lam, lamf, lamo);
+        ctstep<V, LIM, FT1, 0, true, true, false, false, CL_DIRECT, false>(A, X, M, 0, lamh, lam, lamf, lamo);
+        ctstep<V, LIM, FT1, 1, true, true, false, false, CL_DIRECT, false>(A, X, M, 1, lamh, lam, lamf, lamo);
+        ctstep<V, LIM, FT1, 2, true, true, false, false, CL_DIRECT, false>(A, X, M, 2, lamh, lam, lamf, lamo);
+        ctstep<V, LIM, FT1, 3, true, true, true, false, CL_DIRECT, true>(A, X, M, 3, lamh, lam, lamf, lamo);
+        // steady state: the four steps s .. s+3 load interior cells s+1 .. s+4
+#pragma unroll 1
+        for (; s + 4 <= n - 1; s += 4) {
+            ctstep<V, LIM, FT1, 0, true, true, true, true, CL_DIRECT_PF, true>(A, X, M, s, lamh, lam, lamf, lamo);
+            ctstep<V, LIM, FT1, 1, true, true, true, true, CL_DIRECT_PF, true>(A, X, M, s + 1, lamh, lam, lamf, lamo);
+            ctstep<V, LIM, FT1, 2, true, true, true, true, CL_DIRECT_PF, true>(A, X, M, s + 2, lamh, lam, lamf, lamo);
+            ctstep<V, LIM, FT1, 3, true, true, true, true, CL_DIRECT_PF, true>(A, X, M, s + 3, lamh, lam, lamf, lamo);
+        }
+    } else {
+        ctstep<V, LIM, FT1, 3, true, false, false, false, CL_MAPPED, false>(A, X, M, -1, lamh, lam, lamf, lamo);
+        ctstep<V, LIM, FT1, 0, true, true, false, false, CL_MAPPED, false>(A, X, M, 0, lamh, lam, lamf, lamo);
+        ctstep<V, LIM, FT1, 1, true, true, false, false, CL_MAPPED, false>(A, X, M, 1, lamh, lam, lamf, lamo);
+        ctstep<V, LIM, FT1, 2, true, true, false, false, CL_MAPPED, false>(A, X, M, 2, lamh, lam, lamf, lamo);
+        ctstep<V, LIM, FT1, 3, true, true, true, false, CL_MAPPED, true>(A, X, M, 3, lamh, lam, lamf, lamo);
+    }
+    // tail: cells s .. n+3 through the map (n-4 <= s <= n-1 after the loop,
+    // s = 0 mod 4: at most eight cells)
+    if (s <= n + 3) ctstep<V, LIM, FT1, 0, true, true, true, true, CL_MAPPED, true>(A, X, M, s, lamh, lam, lamf, lamo);
+    if (s + 1 <= n + 3) ctstep<V, LIM, FT1, 1, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 1, lamh, lam, lamf, lamo);
+    if (s + 2 <= n + 3) ctstep<V, LIM, FT1, 2, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 2, lamh, lam, lamf, lamo);
+    if (s + 3 <= n + 3) ctstep<V, LIM, FT1, 3, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 3, lamh, lam, lamf, lamo);
+    if (s + 4 <= n + 3) ctstep<V, LIM, FT1, 0, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 4, lamh, lam, lamf, lamo);
+    if (s + 5 <= n + 3) ctstep<V, LIM, FT1, 1, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 5, lamh, lam, lamf, lamo);
+    if (s + 6 <= n + 3) ctstep<V, LIM, FT1, 2, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 6, lamh, lam, lamf, lamo);
+    if (s + 7 <= n + 3) ctstep<V, LIM, FT1, 3, true, true, true, true, CL_NONE, false>(A, X, M, s + 7, lamh, lam, lamf, lamo);
+}
+
+// ---------------------------------------------------------------------------
+// launchers (defined in fish_col_impl.cuh, instantiated per lane-vector type
+// in their own translation units so they compile in parallel)
+// ---------------------------------------------------------------------------
+// L_d with the lane-vector type V: hse selects the hydrostatic correction,
+// ft1 says whether the fast axis is t1 (FP32 callers always order the frame
+// so that it is).  Limiter from A.lim.
+template <class V>
+cudaError_t col_fluid(const ColFluidArgs<typename VT<V>::S> &A, bool hse, bool ft1, cudaStream_t s);
+// B_d with the lane-vector type V.
+template <class V> cudaError_t col_ct(const ColCTArgs<typename VT<V>::S> &A, bool ft1, cudaStream_t s);
+
+}  // namespace fish

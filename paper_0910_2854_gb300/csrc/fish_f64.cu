@@ -1,10 +1,13 @@
 // fish_f64.cu -- FP64 instantiation of the sweep kernels.  Compiled without
 // FMA contraction (-fmad=false) so that every operation rounds like a plain
 // IEEE double evaluation of the paper's formulas, in the order written.
+#include "fish_col_impl.cuh"
 #include "fish_launch.cuh"
 
 namespace fish {
 template struct Launch<double>;
+template cudaError_t col_fluid<double>(const ColFluidArgs<double> &, bool, bool, cudaStream_t);
+template cudaError_t col_ct<double>(const ColCTArgs<double> &, bool, cudaStream_t);
 }
 
 namespace fish {

@@ -422,36 +422,83 @@ template <class T> struct CFLArgs {
     unsigned *flags;
 };
 
+// FP32 signal speeds along the three axes of one cell, sharing the
+// primitives: out[d] = (|v_d| + c_F,d) / h_d (reading C-15), compensated
+// pressure recovery as in the sweeps.
+__device__ __forceinline__ float cfl_rate_f32(const float u[5], const float b[3], float gamma, float gm1,
+                                              const float rh[3], unsigned &flags)
+{
+    const float ri = __fdividef(1.0f, u[0]);
+    const float v[3] = {u[1] * ri, u[2] * ri, u[3] * ri};
+    const float kin = 0.5f * (u[1] * v[0] + u[2] * v[1] + u[3] * v[2]);
+    const float b2[3] = {b[0] * b[0], b[1] * b[1], b[2] * b[2]};
+    const float mag = 0.5f * (b2[0] + b2[1] + b2[2]);
+    const float p = gas_pressure<float>(gm1, u[4], kin, mag);
+    const float a2 = gamma * p * ri;
+    float best = 0.0f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float bn2 = b2[d] * ri;
+        const float bt2 = (b2[(d + 1) % 3] + b2[(d + 2) % 3]) * ri;
+        const float B2 = bn2 + bt2;
+        const float disc = (a2 - B2) * (a2 - B2) + 4.0f * a2 * bt2;
+        const float cf = sqrtf(0.5f * (a2 + B2 + sqrtf(disc)));
+        best = fmaxf(best, (fabsf(v[d]) + cf) * rh[d]);
+        if (cf != cf) flags |= FLAG_NAN;
+    }
+    if (!(u[0] > 0.0f)) flags |= FLAG_RHO;
+    if (!(p > 0.0f)) flags |= FLAG_P;
+    return best;
+}
+
+// CFL minimum over the box: one block per group of rows along the fastest
+// memory axis (no per-cell index division); per-block minimum, then one
+// atomic on the order-preserving bits of the positive double.
 template <class T>
 __global__ void __launch_bounds__(256) cfl_kernel(CFLArgs<T> A)
 {
     const Geom &g = A.g;
-    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
-    double best = 1e300;
+    const int f0 = g.ord[0], f1 = g.ord[1], f2 = g.ord[2];
+    const int nf = g.n[f0], nm = g.n[f1], ns = g.n[f2];
+    const long long rows = (long long)nm * ns;
+    double best = 1e300;   // min of h_d / (|v_d| + c_F,d)
+    float fbest = 0.0f;    // FP32 path: max of (|v_d| + c_F,d) / h_d
     unsigned flags = 0;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
-         idx += (long long)gridDim.x * blockDim.x) {
-        int cc[3];
-        coords_of(g, idx, cc);
-        T bc[3];
+    float rh[3];
+    for (int d = 0; d < 3; ++d) rh[d] = (float)(1.0 / A.h[d]);
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int m = (int)(row % nm), k = (int)(row / nm);
+        const long long rbase = (long long)m * g.st[f1] + (long long)k * g.st[f2];
+        const long long om = (long long)(gmap(m - 1, nm, g.bc) - m) * g.st[f1];
+        const long long ok = (long long)(gmap(k - 1, ns, g.bc) - k) * g.st[f2];
+        for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+            const long long idx = rbase + f;
+            const long long ofm = (long long)(gmap(f - 1, nf, g.bc) - f);
+            T bc[3];
+            bc[f0] = T(0.5) * (__ldg(A.in[5 + f0] + idx + ofm) + __ldg(A.in[5 + f0] + idx));
+            bc[f1] = T(0.5) * (__ldg(A.in[5 + f1] + idx + om) + __ldg(A.in[5 + f1] + idx));
+            bc[f2] = T(0.5) * (__ldg(A.in[5 + f2] + idx + ok) + __ldg(A.in[5 + f2] + idx));
+            if constexpr (sizeof(T) == 8) {
+                // per axis in the paper's frame, the oracle's operation order
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-            const long long lo = idx + (long long)(gmap(cc[ax] - 1, g.n[ax], g.bc) - cc[ax]) * g.st[ax];
-            bc[ax] = T(0.5) * (__ldg(A.in[5 + ax] + lo) + __ldg(A.in[5 + ax] + idx));
-        }
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-            T u[5] = {__ldg(A.in[0] + idx), __ldg(A.in[1 + d] + idx), __ldg(A.in[1 + t1] + idx),
-                      __ldg(A.in[1 + t2] + idx), __ldg(A.in[4] + idx)};
-            T bb[3] = {bc[d], bc[t1], bc[t2]};
-            const T sp = signal_speed<T>(u, bb, A.gamma, A.gm1, flags);
-            // h_d / (|v_d| + c_F,d) in the path's precision; the minimum is
-            // exact, only the final dt = k * min is formed in FP64
-            const double r = (double)div_(T(A.h[d]), sp);
-            best = r < best ? r : best;
+                for (int d = 0; d < 3; ++d) {
+                    const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+                    T u[5] = {__ldg(A.in[0] + idx), __ldg(A.in[1 + d] + idx), __ldg(A.in[1 + t1] + idx),
+                              __ldg(A.in[1 + t2] + idx), __ldg(A.in[4] + idx)};
+                    T bb[3] = {bc[d], bc[t1], bc[t2]};
+                    const T sp = signal_speed<T>(u, bb, A.gamma, A.gm1, flags);
+                    const double r = (double)(T(A.h[d]) / sp);
+                    best = r < best ? r : best;
+                }
+            } else {
+                const float u[5] = {__ldg(A.in[0] + idx), __ldg(A.in[1] + idx), __ldg(A.in[2] + idx),
+                                    __ldg(A.in[3] + idx), __ldg(A.in[4] + idx)};
+                const float b[3] = {(float)bc[0], (float)bc[1], (float)bc[2]};
+                fbest = fmaxf(fbest, cfl_rate_f32(u, b, (float)A.gamma, (float)A.gm1, rh, flags));
+            }
         }
     }
+    if constexpr (sizeof(T) == 4) best = fbest > 0.0f ? 1.0 / (double)fbest : 1e300;
     // block minimum, then one atomic on the order-preserving bits
     for (int off = 16; off > 0; off >>= 1) {
         double o = __shfl_xor_sync(0xffffffffu, best, off);

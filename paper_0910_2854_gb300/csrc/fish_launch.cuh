@@ -2,6 +2,7 @@
 // Included only by the per-precision translation units.
 #pragma once
 
+#include "fish_column.cuh"
 #include "fish_kernels.cuh"
 #include "fish_launch.h"
 
@@ -13,33 +14,77 @@ static inline unsigned grid_for(long long work, int block)
     return (unsigned)(g < 1 ? 1 : g);
 }
 
+// Sweep frame of axis d in the layout of g: the fast transverse axis is the
+// one with unit stride (it must not be d), the other transverse axis the
+// remaining one.
+struct Frame {
+    int d, t1, t2, fast, other;
+    bool ft1;
+    long long sd, so;
+    int n, nf, no;
+};
+
+static inline bool frame_of(const Geom &g, int d, Frame &F)
+{
+    F.d = d;
+    F.t1 = (d + 1) % 3;
+    F.t2 = (d + 2) % 3;
+    F.fast = g.ord[0];
+    if (F.fast == d) return false;
+    F.other = F.fast == F.t1 ? F.t2 : F.t1;
+    F.ft1 = F.fast == F.t1;
+    F.sd = g.st[d];
+    F.so = g.st[F.other];
+    F.n = g.n[d];
+    F.nf = g.n[F.fast];
+    F.no = g.n[F.other];
+    return true;
+}
+
 template <class T>
 cudaError_t Launch<T>::fluid(const T *const in[8], T *const out[5], const T *phi, const double *dt,
                              const Geom &g, int d, int lim, bool hse, double gamma, double alpha,
                              double h, unsigned *flags, cudaStream_t s)
 {
-    FluidArgs<T> A;
-    for (int f = 0; f < 8; ++f) A.in[f] = in[f];
-    for (int f = 0; f < 5; ++f) A.out[f] = out[f];
+    Frame F;
+    if (!frame_of(g, d, F)) return cudaErrorInvalidValue;
+    ColFluidArgs<T> A;
+    // FP32 orders the frame so that t1 is the fast axis (the formulas are
+    // symmetric in t1 and t2); FP64 keeps the cyclic frame of the paper's
+    // rotation so that every sum is added in the plain order
+    const bool swap = sizeof(T) == 4 && !F.ft1;
+    const int a1 = swap ? F.t2 : F.t1, a2 = swap ? F.t1 : F.t2;
+    const int perm[5] = {0, 1 + d, 1 + a1, 1 + a2, 4};
+    for (int k = 0; k < 5; ++k) {
+        A.u[k] = in[perm[k]];
+        A.uo[k] = out[perm[k]];
+    }
+    A.bd = in[5 + d];
+    A.bt1 = in[5 + a1];
+    A.bt2 = in[5 + a2];
     A.phi = phi;
     A.dt = dt;
-    A.g = g;
-    A.d = d;
+    A.sd = F.sd;
+    A.so = F.so;
+    A.n = F.n;
+    A.nf = F.nf;
+    A.no = F.no;
+    A.bc = g.bc;
     A.lim = lim;
     A.gamma = T(gamma);
     A.gm1 = T(gamma - 1.0);
     A.alpha = T(alpha);
     A.h = h;
     A.flags = flags;
-    const long long cols = (long long)g.n[(d + 1) % 3] * g.n[(d + 2) % 3];
-    const unsigned grid = grid_for(cols, 128);
-    if (hse)
-        fluid_sweep_kernel<T, true, true><<<grid, 128, 0, s>>>(A);   // HSE needs the potential
-    else if (phi)
-        fluid_sweep_kernel<T, false, true><<<grid, 128, 0, s>>>(A);
-    else
-        fluid_sweep_kernel<T, false, false><<<grid, 128, 0, s>>>(A);
-    return cudaGetLastError();
+    if constexpr (sizeof(T) == 8) {
+        return col_fluid<double>(A, hse, F.ft1, s);
+    } else {
+        // two columns per thread (packed FP32x2) when the fast extent is even
+#ifndef FISH_FLUID_SCALAR
+        if (F.nf % 2 == 0 && !hse && lim != LIM_NONE) return col_fluid<P2>(A, hse, true, s);
+#endif
+        return col_fluid<float>(A, hse, true, s);
+    }
 }
 
 template <class T>
@@ -47,22 +92,37 @@ cudaError_t Launch<T>::ct(const T *rho, const T *md, const T *const b[3], T *con
                           const double *dt, const Geom &g, int d, int lim, const double h[3],
                           unsigned *flags, cudaStream_t s)
 {
-    CTArgs<T> A;
+    (void)flags;
+    Frame F;
+    if (!frame_of(g, d, F)) return cudaErrorInvalidValue;
+    ColCTArgs<T> A;
     A.rho = rho;
     A.md = md;
-    for (int f = 0; f < 3; ++f) {
-        A.b[f] = b[f];
-        A.bout[f] = bout[f];
-        A.h[f] = h[f];
-    }
+    A.bd = b[d];
+    A.bf = b[F.fast];
+    A.bo = b[F.other];
+    A.bdo = bout[d];
+    A.bfo = bout[F.fast];
+    A.boo = bout[F.other];
     A.dt = dt;
-    A.g = g;
-    A.d = d;
+    A.sd = F.sd;
+    A.so = F.so;
+    A.n = F.n;
+    A.nf = F.nf;
+    A.no = F.no;
+    A.bc = g.bc;
     A.lim = lim;
-    A.flags = flags;
-    const long long cols = (long long)g.n[(d + 1) % 3] * g.n[(d + 2) % 3];
-    ct_sweep_kernel<T><<<grid_for(cols, 128), 128, 0, s>>>(A);
-    return cudaGetLastError();
+    A.h = h[d];
+    A.hf = h[F.fast];
+    A.ho = h[F.other];
+    if constexpr (sizeof(T) == 8) {
+        return col_ct<double>(A, F.ft1, s);
+    } else {
+#ifdef FISH_CT_PAIRS
+        if (F.nf % 2 == 0 && lim != LIM_NONE) return col_ct<P2>(A, true, s);
+#endif
+        return col_ct<float>(A, true, s);
+    }
 }
 
 template <class T>
@@ -77,9 +137,9 @@ cudaError_t Launch<T>::cfl(const T *const in[8], const Geom &g, const double h[3
     A.gm1 = T(gamma - 1.0);
     A.minbits = minbits;
     A.flags = flags;
-    const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
-    unsigned grid = grid_for(N, 256);
-    if (grid > 152u * 16u) grid = 152u * 16u;
+    // one block per row of the fastest axis, at most 8 resident blocks per SM
+    const long long rows = (long long)g.n[g.ord[1]] * g.n[g.ord[2]];
+    const unsigned grid = (unsigned)(rows < 152ll * 8 ? rows : 152ll * 8);
     cfl_kernel<T><<<grid, 256, 0, s>>>(A);
     return cudaGetLastError();
 }

@@ -187,6 +187,46 @@ def test_fp32_path_against_fp64_oracle(F):
     gb.close()
 
 
+FP32_BOXES = {
+    # even fast extents: two columns per thread (packed FP32x2) in every sweep
+    "even_periodic": lambda: W.random_smooth(32, 24, 20, seed=31, h=(0.03, 0.04, 0.05)),
+    # odd x extent: one column per thread in the y and z sweeps, pairs in x
+    "odd_outflow": lambda: W.random_smooth(21, 18, 13, seed=32, bc=W.BC_OUTFLOW),
+    # short pencils (n < 8): prologue and tail only
+    "short": lambda: W.random_smooth(6, 4, 7, seed=33),
+}
+
+
+@pytest.mark.parametrize("box", sorted(FP32_BOXES))
+@pytest.mark.parametrize("lim", [0, 1, 2])
+@pytest.mark.parametrize("op", ["fluid", "ct"])
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_single_operator_fp32(F, box, lim, op, d):
+    """One operator of the FP32 path against the FP64 oracle: 1e-5 relative
+    to each field's largest magnitude, per cell."""
+    w = FP32_BOXES[box]()
+    ob, gb = pair(F, w, precision="fp32", limiter=lim)
+    dt = 0.4 * ob.cfl(1.0)
+    getattr(ob, op)(d, dt)
+    getattr(gb, op)(d, dt)
+    assert rel_err(gb.get_state(), ob.state) <= 1e-5
+    gb.close()
+
+
+@pytest.mark.parametrize("hse", [False, True])
+def test_gravity_fp32(F, hse):
+    """Unsplit gravity (two-column kernels) and the hydrostatic correction
+    (one-column kernels) in FP32 against the oracle after two steps."""
+    w = W.polytrope(24)
+    ob, gb = pair(F, w, precision="fp32", hse=hse)
+    for _ in range(2):
+        dt = ob.cfl(0.5)
+        ob.step(dt)
+        gb.step(dt)
+    assert rel_err(gb.get_state(), ob.state) <= 1e-5
+    gb.close()
+
+
 def test_nonphysical_state_reported(F):
     """A negative-pressure input is reported as FISH_ERR_NONPHYSICAL at the
     next synchronising call (made on the host: no GPU fault involved)."""
