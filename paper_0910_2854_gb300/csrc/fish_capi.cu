@@ -61,6 +61,9 @@ struct fish_ctx {
     double gk = -1.0;
     int gparity = -1;
     bool gdirty = true;
+    bool gfused = false;       // the graph's last sweep reduces the next CFL
+    long long glaunches = 0;   // kernels per graph replay
+    bool cfl_pending = false;  // minbits holds the CFL minimum of the current state
 
     long long launches = 0;
     std::string err;
@@ -227,7 +230,7 @@ int check_flags(fish_ctx *c)
 
 // ---- operators -------------------------------------------------------------
 
-template <class T> int op_fluid(fish_ctx *c, int d)
+template <class T> int op_fluid(fish_ctx *c, int d, bool fuse_cfl)
 {
     const T *in[8];
     T *out[5];
@@ -238,8 +241,8 @@ template <class T> int op_fluid(fish_ctx *c, int d)
     for (int f = 0; f < 3; ++f) in[5 + f] = (const T *)c->bf[c->cb][f];
     FISH_CK(c,
             Launch<T>::fluid(in, out, c->has_phi ? (const T *)(c->layout ? c->phiT : c->phi) : nullptr, c->dt_dev,
-                             geom(c), d, c->lim,
-                             c->hse != 0, c->gamma, c->alpha, c->h[d], c->flags, c->stream),
+                             geom(c), d, c->lim, c->hse != 0, c->gamma, c->alpha, c->h, c->flags,
+                             fuse_cfl ? c->minbits : nullptr, c->stream),
             "fluid sweep launch");
     c->cu = 1 - c->cu;
     c->launches += 1;
@@ -263,17 +266,26 @@ template <class T> int op_ct(fish_ctx *c, int d)
     return FISH_OK;
 }
 
-int apply_op(fish_ctx *c, int op, int d)
+int apply_op(fish_ctx *c, int op, int d, bool fuse_cfl = false)
 {
     int r = set_layout(c, layout_for(d));
     if (r) return r;
     if (c->prec == FISH_PREC_FP64)
-        return op == FISH_OP_FLUID ? op_fluid<double>(c, d) : op_ct<double>(c, d);
-    return op == FISH_OP_FLUID ? op_fluid<float>(c, d) : op_ct<float>(c, d);
+        return op == FISH_OP_FLUID ? op_fluid<double>(c, d, fuse_cfl) : op_ct<double>(c, d);
+    return op == FISH_OP_FLUID ? op_fluid<float>(c, d, fuse_cfl) : op_ct<float>(c, d);
 }
 
-// The twelve operators of one double step in time order (reading C-4).
-int queue_sweeps(fish_ctx *c)
+// Whether the last sweep of a double step (L_x) can also reduce the CFL
+// minimum of the new state (FP32 two-column kernels only).
+bool last_sweep_fuses_cfl(const fish_ctx *c)
+{
+    if (c->prec != FISH_PREC_FP32) return false;
+    return Launch<float>::fluid_fuses_cfl(geom_of(c, layout_for(0)), 0, c->lim, c->hse != 0);
+}
+
+// The twelve operators of one double step in time order (reading C-4);
+// with fuse_cfl the final L_x also reduces the CFL minimum of the result.
+int queue_sweeps(fish_ctx *c, bool fuse_cfl = false)
 {
     int r;
     for (int d = 0; d < 3; ++d) {
@@ -282,7 +294,7 @@ int queue_sweeps(fish_ctx *c)
     }
     for (int d = 2; d >= 0; --d) {
         if ((r = apply_op(c, FISH_OP_CT, d))) return r;
-        if ((r = apply_op(c, FISH_OP_FLUID, d))) return r;
+        if ((r = apply_op(c, FISH_OP_FLUID, d, fuse_cfl && d == 0))) return r;
     }
     return FISH_OK;
 }
@@ -296,9 +308,17 @@ template <class T> int queue_cfl(fish_ctx *c)
     return FISH_OK;
 }
 
+// Standalone CFL reduction into minbits (reset first).
+int queue_cfl_min(fish_ctx *c)
+{
+    FISH_CK(c, fish::launch_reset_min(c->minbits, c->stream), "cfl reset launch");
+    c->launches += 1;
+    return c->prec == FISH_PREC_FP64 ? queue_cfl<double>(c) : queue_cfl<float>(c);
+}
+
 int queue_cfl_dt(fish_ctx *c, double k, double *dt_target, double *dt_copy)
 {
-    int r = c->prec == FISH_PREC_FP64 ? queue_cfl<double>(c) : queue_cfl<float>(c);
+    int r = queue_cfl_min(c);
     if (r) return r;
     FISH_CK(c, fish::launch_cfl_finish(c->minbits, k, dt_target, dt_copy, c->stream), "cfl finish launch");
     c->launches += 1;
@@ -379,6 +399,7 @@ int fish_set_option(fish_ctx *c, int key, double v)
         return fail(c, FISH_ERR_ARG, "unknown option key");
     }
     c->gdirty = true;
+    c->cfl_pending = false;
     return FISH_OK;
 }
 
@@ -406,6 +427,7 @@ int fish_set_state(fish_ctx *c, const double *state)
     if (!c || !state) return FISH_ERR_ARG;
     int r = ensure_alloc(c);
     if (r) return r;
+    c->cfl_pending = false;
     c->layout = 0;
     if (c->prec == FISH_PREC_FP64) {
         for (int f = 0; f < 8; ++f)
@@ -433,6 +455,7 @@ int fish_set_state_device(fish_ctx *c, const void *state, int dtype)
     if (!c || !state || (dtype != FISH_F64 && dtype != FISH_F32)) return FISH_ERR_ARG;
     int r = ensure_alloc(c);
     if (r) return r;
+    c->cfl_pending = false;
     c->layout = 0;
     for (int f = 0; f < 8; ++f) {
         void *dst = field_ptr(c, f);
@@ -460,6 +483,7 @@ int fish_set_state_host(fish_ctx *c, const void *state, int dtype)
     if (dtype == FISH_F64) return fish_set_state(c, (const double *)state);
     int r = ensure_alloc(c);
     if (r) return r;
+    c->cfl_pending = false;
     c->layout = 0;
     if (c->prec == FISH_PREC_FP32) {
         for (int f = 0; f < 8; ++f)
@@ -532,6 +556,7 @@ int fish_cfl_dt(fish_ctx *c, double k, double *dt_out)
 {
     int r = ready(c);
     if (r) return r;
+    c->cfl_pending = false;
     if (!dt_out || !(k > 0.0)) return fail(c, FISH_ERR_ARG, "bad CFL arguments");
     if ((r = queue_cfl_dt(c, k, c->partial, nullptr))) return r;
     FISH_CK(c, cudaMemcpyAsync(dt_out, c->partial, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "dt");
@@ -542,6 +567,7 @@ int fish_step(fish_ctx *c, double dt)
 {
     int r = ready(c);
     if (r) return r;
+    c->cfl_pending = false;
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, FISH_ERR_ARG, "dt must be > 0");
     FISH_CK(c, fish::launch_set_scalar(c->dt_dev, dt, c->stream), "dt");
     FISH_CK(c, fish::launch_set_scalar(c->dt_last, dt, c->stream), "dt");
@@ -554,21 +580,31 @@ int fish_step_cfl(fish_ctx *c, double k, int nsteps)
     int r = ready(c);
     if (r) return r;
     if (!(k > 0.0) || nsteps < 0) return fail(c, FISH_ERR_ARG, "bad arguments");
+    if (nsteps == 0) return FISH_OK;
     // every replay starts (and ends) in the layout of the x sweeps
     if ((r = set_layout(c, layout_for(0)))) return r;
     const int parity = c->cu * 2 + c->cb;
-    if (c->gdirty || !c->gexec || c->gk != k || c->gparity != parity) {
+    const bool fused = last_sweep_fuses_cfl(c);
+    if (c->gdirty || !c->gexec || c->gk != k || c->gparity != parity || c->gfused != fused) {
         if (c->gexec) {
             cudaGraphExecDestroy(c->gexec);
             c->gexec = nullptr;
         }
-        // capture one double step on a capturable stream
+        // capture one double step: dt from the CFL minimum (reduced by the
+        // previous replay's last sweep when fused, else by a CFL pass at the
+        // start), then the twelve operators
         cudaStream_t cap = c->stream;
         cudaGraph_t graph = nullptr;
         const long long l0 = c->launches;
         FISH_CK(c, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
-        r = queue_cfl_dt(c, k, c->dt_dev, c->dt_last);
-        if (!r) r = queue_sweeps(c);
+        if (fused) {
+            cudaError_t e0 = fish::launch_cfl_finish(c->minbits, k, c->dt_dev, c->dt_last, cap);
+            r = e0 == cudaSuccess ? FISH_OK : cuda_fail(c, e0, "cfl finish launch");
+            c->launches += 1;
+        } else {
+            r = queue_cfl_dt(c, k, c->dt_dev, c->dt_last);
+        }
+        if (!r) r = queue_sweeps(c, fused);
         cudaError_t e = cudaStreamEndCapture(cap, &graph);
         if (r) {
             if (graph) cudaGraphDestroy(graph);
@@ -578,15 +614,22 @@ int fish_step_cfl(fish_ctx *c, double k, int nsteps)
         e = cudaGraphInstantiate(&c->gexec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+        c->glaunches = c->launches - l0;
         c->launches = l0;  // captured, not launched
         c->gk = k;
         c->gparity = parity;
+        c->gfused = fused;
         c->gdirty = false;
+    }
+    if (fused && !c->cfl_pending) {
+        // the CFL minimum of the current state for the first replay
+        if ((r = queue_cfl_min(c))) return r;
     }
     for (int s = 0; s < nsteps; ++s) {
         FISH_CK(c, cudaGraphLaunch(c->gexec, c->stream), "graph launch");
-        c->launches += 16;
+        c->launches += c->glaunches;
     }
+    c->cfl_pending = fused;
     return FISH_OK;
 }
 
@@ -603,6 +646,7 @@ int fish_apply(fish_ctx *c, int op, int dir, double dt)
 {
     int r = ready(c);
     if (r) return r;
+    c->cfl_pending = false;
     if ((op != FISH_OP_FLUID && op != FISH_OP_CT) || dir < 0 || dir > 2 || !(dt > 0.0))
         return fail(c, FISH_ERR_ARG, "bad operator arguments");
     FISH_CK(c, fish::launch_set_scalar(c->dt_dev, dt, c->stream), "dt");

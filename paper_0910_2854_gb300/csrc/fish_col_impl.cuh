@@ -18,6 +18,13 @@ template <class V, bool HSE, bool GRAV, int LIM, bool FT1>
 static cudaError_t col_fluid_launch(const ColFluidArgs<typename VT<V>::S> &A, cudaStream_t s)
 {
     const long long cols = (long long)(A.nf / VT<V>::W) * A.no;
+    if constexpr (std::is_same<V, P2>::value && !HSE) {
+        if (A.cfl_min) {
+            fluid_col_kernel<V, HSE, GRAV, LIM, FT1, true><<<col_grid(cols, 128), 128, 0, s>>>(A);
+            return cudaGetLastError();
+        }
+    }
+    if (A.cfl_min) return cudaErrorInvalidValue;  // only the two-column kernels carry the CFL epilogue
     fluid_col_kernel<V, HSE, GRAV, LIM, FT1><<<col_grid(cols, 128), 128, 0, s>>>(A);
     return cudaGetLastError();
 }

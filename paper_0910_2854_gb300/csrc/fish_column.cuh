@@ -42,6 +42,12 @@ template <class S> struct ColFluidArgs {
     S gamma, gm1, alpha;
     double h;               // cell width along d
     unsigned *flags;
+    // CFL of the updated state (kernels built with CFLF): the maximum over the
+    // output cells of (|v_a| + c_F,a) / h_a over the three axes a in the frame
+    // order (d, t1, t2) goes to *cfl_min as the order-preserving bits of its
+    // reciprocal (atomic minimum)
+    unsigned long long *cfl_min;
+    S rh[3];
 };
 
 template <class S> struct ColCTArgs {
@@ -283,6 +289,31 @@ __device__ __forceinline__ void cflux2(const CCell<V> &c0, const CCell<V> &c1, c
     }
 }
 
+// Largest (|v_a| + c_F,a) / h_a over the three axes of the frame (eq0083-
+// eq0084, reading C-15) for a cell with conserved state u and cell-centred
+// field b; the primitives are shared between the axes (FP32 path).
+template <class V>
+__device__ __forceinline__ V cfl_rate3(const V u[5], const V b[3], V gamma, V gm1, const V rh[3])
+{
+    const V half = vb<V>(0.5f);
+    const V ri = vrcp(u[0]);
+    const V v0 = u[1] * ri, v1 = u[2] * ri, v2 = u[3] * ri;
+    const V kin = half * vfma(u[3], v2, vfma(u[2], v1, u[1] * v0));
+    const V q0 = b[0] * b[0], q1 = b[1] * b[1], q2 = b[2] * b[2];
+    const V mag = half * (q0 + q1 + q2);
+    const V p = gm1 * eint_comp(u[4], kin, mag);
+    const V a2 = gamma * p * ri;
+    const V B2 = (q0 + q1 + q2) * ri;
+    const V am = a2 - B2;
+    const V c0 = am * am;
+    const V aB = a2 + B2;
+    const V f4a2 = vb<V>(4.0f) * a2;
+    const V r0 = (vabs(v0) + vsqrt(half * (aB + vsqrt(vfma(f4a2, (q1 + q2) * ri, c0))))) * rh[0];
+    const V r1 = (vabs(v1) + vsqrt(half * (aB + vsqrt(vfma(f4a2, (q0 + q2) * ri, c0))))) * rh[1];
+    const V r2 = (vabs(v2) + vsqrt(half * (aB + vsqrt(vfma(f4a2, (q0 + q1) * ri, c0))))) * rh[2];
+    return vmax(vmax(r0, r1), r2);
+}
+
 // ---------------------------------------------------------------------------
 // L_d: fluid column march
 // ---------------------------------------------------------------------------
@@ -307,6 +338,7 @@ template <class V> struct FMarch {
     V F2[2][5];          // corrector fluxes
     V phm2;              // potential of raw cell r-2
     Checks<V> chk;
+    V cflr;              // largest CFL rate of the output cells (CFLF)
 };
 
 template <class S> struct FCtx {
@@ -384,7 +416,7 @@ enum : int { LD_NONE = 0, LD_DIRECT = 1, LD_MAPPED = 2, LD_DIRECT_PF = 3 };
 // One step of the march for raw cell r (K = r mod 4).  The raw data of cell
 // r is in M.R on entry (loaded by the previous step); the step loads raw
 // cell r+1 (kind LD) into M.R.  FT1: the fast axis is t1 (else t2).
-template <class V, bool HSE, bool GRAV, int LIM, bool FT1, int K, int ST, int LD>
+template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool CFLF, int K, int ST, int LD>
 __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S> &X,
                                       FMarch<V> &M, int r, V lam, V lamh, V hdt, V dt, V rtwoh)
 {
@@ -474,6 +506,21 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
                 }
 #pragma unroll
                 for (int k = 0; k < 5; ++k) vstore(A.uo[k], io, un[k]);
+                if constexpr (CFLF) {
+                    // CFL rate of the updated cell with its cell-centred field
+                    const auto *bfp = FT1 ? A.bt1 : A.bt2;
+                    const auto *bop = FT1 ? A.bt2 : A.bt1;
+                    const long long iom = X.base + (long long)(o > 0 ? o - 1 : gmap(-1, A.n, A.bc)) * A.sd;
+                    V bc[3];
+                    bc[0] = half * (vload<V>(A.bd, iom) + vload<V>(A.bd, io));
+                    const V bfv = vload<V>(bfp, io);
+                    const V bfc = half * (vshift_lo(__ldg(bfp + io + X.ofm), bfv) + bfv);
+                    const V boc = half * (vload<V>(bop, io + X.oom) + vload<V>(bop, io));
+                    bc[FT1 ? 1 : 2] = bfc;
+                    bc[FT1 ? 2 : 1] = boc;
+                    const V rh[3] = {vb<V>(A.rh[0]), vb<V>(A.rh[1]), vb<V>(A.rh[2])};
+                    M.cflr = vmax(M.cflr, cfl_rate3<V>(un, bc, vb<V>(A.gamma), vb<V>(A.gm1), rh));
+                }
             }
         }
     }
@@ -489,16 +536,16 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
 
 // L_d over all columns.  The prologue runs raw cells -3 .. 2 (K = 1, 2, 3,
 // 0, 1, 2); boxes with n < 8 load everything through the map.
-template <class V, bool HSE, bool GRAV, int LIM, bool FT1, int PLD>
+template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool CFLF, int PLD>
 __device__ __forceinline__ void fprologue(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S> &X,
                                           FMarch<V> &M, V lam, V lamh, V hdt, V dt, V rtwoh)
 {
-    fstep<V, HSE, GRAV, LIM, FT1, 1, 0, LD_MAPPED>(A, X, M, -3, lam, lamh, hdt, dt, rtwoh);
-    fstep<V, HSE, GRAV, LIM, FT1, 2, ST_F1, LD_MAPPED>(A, X, M, -2, lam, lamh, hdt, dt, rtwoh);
-    fstep<V, HSE, GRAV, LIM, FT1, 3, ST_F1 | ST_PRED, PLD>(A, X, M, -1, lam, lamh, hdt, dt, rtwoh);
-    fstep<V, HSE, GRAV, LIM, FT1, 0, ST_F1 | ST_PRED, PLD>(A, X, M, 0, lam, lamh, hdt, dt, rtwoh);
-    fstep<V, HSE, GRAV, LIM, FT1, 1, ST_F1 | ST_PRED, PLD>(A, X, M, 1, lam, lamh, hdt, dt, rtwoh);
-    fstep<V, HSE, GRAV, LIM, FT1, 2, ST_F1 | ST_PRED | ST_F2, PLD>(A, X, M, 2, lam, lamh, hdt, dt, rtwoh);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, 1, 0, LD_MAPPED>(A, X, M, -3, lam, lamh, hdt, dt, rtwoh);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, 2, ST_F1, LD_MAPPED>(A, X, M, -2, lam, lamh, hdt, dt, rtwoh);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, 3, ST_F1 | ST_PRED, PLD>(A, X, M, -1, lam, lamh, hdt, dt, rtwoh);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, 0, ST_F1 | ST_PRED, PLD>(A, X, M, 0, lam, lamh, hdt, dt, rtwoh);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, 1, ST_F1 | ST_PRED, PLD>(A, X, M, 1, lam, lamh, hdt, dt, rtwoh);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, 2, ST_F1 | ST_PRED | ST_F2, PLD>(A, X, M, 2, lam, lamh, hdt, dt, rtwoh);
 }
 
 #ifndef FISH_COL_MINB
@@ -508,7 +555,7 @@ __device__ __forceinline__ void fprologue(const ColFluidArgs<typename VT<V>::S> 
 #define FISH_COL_MINB1 3   // one-column FP32 kernels
 #endif
 
-template <class V, bool HSE, bool GRAV, int LIM, bool FT1>
+template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool CFLF = false>
 __global__ void __launch_bounds__(128, VT<V>::F64 ? 1 : (VT<V>::W == 2 || HSE ? FISH_COL_MINB : FISH_COL_MINB1))
     fluid_col_kernel(const ColFluidArgs<typename VT<V>::S> A)
 {
@@ -533,35 +580,53 @@ __global__ void __launch_bounds__(128, VT<V>::F64 ? 1 : (VT<V>::W == 2 || HSE ? 
 
     FMarch<V> M;
     checks_init(M.chk);
+    M.cflr = vb<V>(0.0f);
     M.phm2 = vb<V>(0.0f);
     M.ph[0] = M.ph[1] = vb<V>(0.0f);
     fload_mapped<V, GRAV, FT1>(A, X, -3, M.R);
     constexpr int ALL = ST_F1 | ST_PRED | ST_F2 | ST_OUT;
     int r = 3;
     if (n >= 8) {
-        fprologue<V, HSE, GRAV, LIM, FT1, LD_DIRECT>(A, X, M, lam, lamh, hdt, dt, rtwoh);
+        fprologue<V, HSE, GRAV, LIM, FT1, CFLF, LD_DIRECT>(A, X, M, lam, lamh, hdt, dt, rtwoh);
         // steady state: the four steps r .. r+3 prefetch interior cells
 #pragma unroll 1
         for (; r + 4 <= n - 1; r += 4) {
-            fstep<V, HSE, GRAV, LIM, FT1, 3, ALL, LD_DIRECT_PF>(A, X, M, r, lam, lamh, hdt, dt, rtwoh);
-            fstep<V, HSE, GRAV, LIM, FT1, 0, ALL, LD_DIRECT_PF>(A, X, M, r + 1, lam, lamh, hdt, dt, rtwoh);
-            fstep<V, HSE, GRAV, LIM, FT1, 1, ALL, LD_DIRECT_PF>(A, X, M, r + 2, lam, lamh, hdt, dt, rtwoh);
-            fstep<V, HSE, GRAV, LIM, FT1, 2, ALL, LD_DIRECT_PF>(A, X, M, r + 3, lam, lamh, hdt, dt, rtwoh);
+            fstep<V, HSE, GRAV, LIM, FT1, CFLF, 3, ALL, LD_DIRECT_PF>(A, X, M, r, lam, lamh, hdt, dt, rtwoh);
+            fstep<V, HSE, GRAV, LIM, FT1, CFLF, 0, ALL, LD_DIRECT_PF>(A, X, M, r + 1, lam, lamh, hdt, dt, rtwoh);
+            fstep<V, HSE, GRAV, LIM, FT1, CFLF, 1, ALL, LD_DIRECT_PF>(A, X, M, r + 2, lam, lamh, hdt, dt, rtwoh);
+            fstep<V, HSE, GRAV, LIM, FT1, CFLF, 2, ALL, LD_DIRECT_PF>(A, X, M, r + 3, lam, lamh, hdt, dt, rtwoh);
         }
     } else {
-        fprologue<V, HSE, GRAV, LIM, FT1, LD_MAPPED>(A, X, M, lam, lamh, hdt, dt, rtwoh);
+        fprologue<V, HSE, GRAV, LIM, FT1, CFLF, LD_MAPPED>(A, X, M, lam, lamh, hdt, dt, rtwoh);
     }
     // tail: raw cells r .. n+2 (r = 3 mod 4, at most seven), loads through
     // the map (harmless beyond n+2)
-    if (r <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, 3, ALL, LD_MAPPED>(A, X, M, r, lam, lamh, hdt, dt, rtwoh);
-    if (r + 1 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, 0, ALL, LD_MAPPED>(A, X, M, r + 1, lam, lamh, hdt, dt, rtwoh);
-    if (r + 2 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, 1, ALL, LD_MAPPED>(A, X, M, r + 2, lam, lamh, hdt, dt, rtwoh);
-    if (r + 3 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, 2, ALL, LD_MAPPED>(A, X, M, r + 3, lam, lamh, hdt, dt, rtwoh);
-    if (r + 4 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, 3, ALL, LD_MAPPED>(A, X, M, r + 4, lam, lamh, hdt, dt, rtwoh);
-    if (r + 5 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, 0, ALL, LD_MAPPED>(A, X, M, r + 5, lam, lamh, hdt, dt, rtwoh);
-    if (r + 6 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, 1, ALL, LD_NONE>(A, X, M, r + 6, lam, lamh, hdt, dt, rtwoh);
+    if (r <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, 3, ALL, LD_MAPPED>(A, X, M, r, lam, lamh, hdt, dt, rtwoh);
+    if (r + 1 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, 0, ALL, LD_MAPPED>(A, X, M, r + 1, lam, lamh, hdt, dt, rtwoh);
+    if (r + 2 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, 1, ALL, LD_MAPPED>(A, X, M, r + 2, lam, lamh, hdt, dt, rtwoh);
+    if (r + 3 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, 2, ALL, LD_MAPPED>(A, X, M, r + 3, lam, lamh, hdt, dt, rtwoh);
+    if (r + 4 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, 3, ALL, LD_MAPPED>(A, X, M, r + 4, lam, lamh, hdt, dt, rtwoh);
+    if (r + 5 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, 0, ALL, LD_MAPPED>(A, X, M, r + 5, lam, lamh, hdt, dt, rtwoh);
+    if (r + 6 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, 1, ALL, LD_NONE>(A, X, M, r + 6, lam, lamh, hdt, dt, rtwoh);
     const unsigned fl = checks_flags(M.chk);
     if (fl) atomicOr(A.flags, fl);
+    if constexpr (CFLF) {
+        // warp maximum of the rates (order-preserving bits of non-negative
+        // floats), then one atomic minimum of 1/rate per warp
+        float m = 0.0f;
+#pragma unroll
+        for (int i = 0; i < VT<V>::W; ++i) m = fmaxf(m, (float)vget(M.cflr, i));
+        const unsigned mask = __activemask();
+        const unsigned wm = __reduce_max_sync(mask, __float_as_uint(m));
+        if ((threadIdx.x & 31) == __ffs(mask) - 1) {
+            const float mx = __uint_as_float(wm);
+            if (mx > 0.0f && mx == mx) {
+                atomicMin(A.cfl_min, (unsigned long long)__double_as_longlong(1.0 / (double)mx));
+            } else {
+                atomicOr(A.flags, FLAG_NAN);
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------

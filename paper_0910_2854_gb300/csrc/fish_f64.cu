@@ -18,6 +18,14 @@ cudaError_t launch_cfl_finish(unsigned long long *minbits, double k, double *dt,
     return cudaGetLastError();
 }
 
+static __global__ void reset_min_kernel(unsigned long long *p) { *p = 0x7FF0000000000000ull; }
+
+cudaError_t launch_reset_min(unsigned long long *minbits, cudaStream_t s)
+{
+    reset_min_kernel<<<1, 1, 0, s>>>(minbits);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_set_scalar(double *p, double v, cudaStream_t s)
 {
     set_scalar_kernel<<<1, 1, 0, s>>>(p, v);

@@ -41,13 +41,32 @@ static inline bool frame_of(const Geom &g, int d, Frame &F)
     return true;
 }
 
+// The two-column FP32 kernels are used for even fast extents without the
+// hydrostatic correction and with a limiter.
+template <class T> static bool uses_pairs(const Frame &F, int lim, bool hse)
+{
+#ifdef FISH_FLUID_SCALAR
+    return false;
+#else
+    return sizeof(T) == 4 && F.nf % 2 == 0 && !hse && lim != LIM_NONE;
+#endif
+}
+
+template <class T> bool Launch<T>::fluid_fuses_cfl(const Geom &g, int d, int lim, bool hse)
+{
+    Frame F;
+    return frame_of(g, d, F) && uses_pairs<T>(F, lim, hse);
+}
+
 template <class T>
 cudaError_t Launch<T>::fluid(const T *const in[8], T *const out[5], const T *phi, const double *dt,
                              const Geom &g, int d, int lim, bool hse, double gamma, double alpha,
-                             double h, unsigned *flags, cudaStream_t s)
+                             const double h3[3], unsigned *flags, unsigned long long *cfl_min, cudaStream_t s)
 {
     Frame F;
     if (!frame_of(g, d, F)) return cudaErrorInvalidValue;
+    if (cfl_min && !uses_pairs<T>(F, lim, hse)) return cudaErrorInvalidValue;
+    const double h = h3[d];
     ColFluidArgs<T> A;
     // FP32 orders the frame so that t1 is the fast axis (the formulas are
     // symmetric in t1 and t2); FP64 keeps the cyclic frame of the paper's
@@ -76,13 +95,15 @@ cudaError_t Launch<T>::fluid(const T *const in[8], T *const out[5], const T *phi
     A.alpha = T(alpha);
     A.h = h;
     A.flags = flags;
+    A.cfl_min = cfl_min;
+    A.rh[0] = T(1.0 / h3[d]);
+    A.rh[1] = T(1.0 / h3[a1]);
+    A.rh[2] = T(1.0 / h3[a2]);
     if constexpr (sizeof(T) == 8) {
         return col_fluid<double>(A, hse, F.ft1, s);
     } else {
         // two columns per thread (packed FP32x2) when the fast extent is even
-#ifndef FISH_FLUID_SCALAR
-        if (F.nf % 2 == 0 && !hse && lim != LIM_NONE) return col_fluid<P2>(A, hse, true, s);
-#endif
+        if (uses_pairs<T>(F, lim, hse)) return col_fluid<P2>(A, hse, true, s);
         return col_fluid<float>(A, hse, true, s);
     }
 }

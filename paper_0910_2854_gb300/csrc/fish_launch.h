@@ -11,9 +11,13 @@ namespace fish {
 
 template <class T> struct Launch {
     // L_d: in[8] current state, out[5] fluid fields of the other buffer.
+    // With cfl_min, the sweep also reduces the CFL rate of its output state
+    // (all three axes, cell widths h3) into *cfl_min (only where
+    // fluid_fuses_cfl says so).
     static cudaError_t fluid(const T *const in[8], T *const out[5], const T *phi, const double *dt,
                              const Geom &g, int d, int lim, bool hse, double gamma, double alpha,
-                             double h, unsigned *flags, cudaStream_t s);
+                             const double h3[3], unsigned *flags, unsigned long long *cfl_min, cudaStream_t s);
+    static bool fluid_fuses_cfl(const Geom &g, int d, int lim, bool hse);
     // B_d: rho, m_d of the current state; b[3] current field, bout[3] other.
     static cudaError_t ct(const T *rho, const T *md, const T *const b[3], T *const bout[3],
                           const double *dt, const Geom &g, int d, int lim, const double h[3],
@@ -36,5 +40,7 @@ template <class T> struct Launch {
 cudaError_t launch_cfl_finish(unsigned long long *minbits, double k, double *dt, double *dt_copy,
                               cudaStream_t s);
 cudaError_t launch_set_scalar(double *p, double v, cudaStream_t s);
+// reset a CFL minimum to +infinity before a reduction
+cudaError_t launch_reset_min(unsigned long long *minbits, cudaStream_t s);
 
 }  // namespace fish

@@ -133,6 +133,31 @@ def test_cfl_and_graph_step_match_host_loop(F):
     gb2.close()
 
 
+def test_fp32_graph_with_cfl_in_last_sweep(F):
+    """FP32 even box: the graph's last sweep reduces the next step's CFL
+    minimum.  Time steps and state follow the oracle's host loop to 1e-5;
+    a replay split over two calls equals one call bitwise."""
+    w = W.random_smooth(32, 24, 20, seed=14, h=(0.03, 0.04, 0.05))
+    ob, gb = pair(F, w, precision="fp32")
+    _, gb2 = pair(F, w, precision="fp32")
+    dts = []
+    for _ in range(5):
+        dts.append(ob.cfl(0.5))
+        ob.step(dts[-1])
+    gb.step_cfl(0.5, 5)
+    assert abs(gb.last_dt() - dts[-1]) <= 1e-5 * dts[-1]
+    assert rel_err(gb.get_state(), ob.state) <= 1e-5
+    gb2.step_cfl(0.5, 2)
+    gb2.step_cfl(0.5, 3)
+    assert np.array_equal(gb2.get_state(), gb.get_state())
+    # a host CFL in between forces a fresh reduction; dt stays consistent
+    d = gb2.cfl_dt(0.5)
+    gb2.step_cfl(0.5, 1)
+    assert abs(gb2.last_dt() - d) <= 1e-6 * d
+    gb.close()
+    gb2.close()
+
+
 def test_diagnostics_conservation_and_divergence(F):
     w = W.random_smooth(24, 22, 20, seed=9)
     ob, gb = pair(F, w)
