@@ -46,8 +46,9 @@ struct fish_ctx {
     void *bf[2][3] = {};   // face fields b_x, b_y, b_z (two buffers)
     int cu = 0, cb = 0;    // current buffer of each group
     int layout = 0;        // 0: x fastest (y, z sweeps); 1: y fastest (x sweeps)
-    void *phi = nullptr;   // potential, x-fastest layout
-    void *phiT = nullptr;  // potential, y-fastest layout
+    void *phi = nullptr;   // FP64: potential, x-fastest layout
+    void *phiT = nullptr;  // FP64: potential, y-fastest layout
+    void *phiD[3] = {};    // FP32: phi(next cell along d) - phi(cell) formed in FP64, in the layout of the d sweeps
     bool has_phi = false;
 
     double *dt_dev = nullptr;       // time step read by the sweep kernels
@@ -230,6 +231,15 @@ int check_flags(fish_ctx *c)
 
 // ---- operators -------------------------------------------------------------
 
+// Potential data of the d sweep: FP64 the cell potential in the current
+// layout, FP32 the FP64-formed differences along d.
+template <class T> const T *sweep_potential(const fish_ctx *c, int d)
+{
+    if (!c->has_phi) return nullptr;
+    if (sizeof(T) == 4) return (const T *)c->phiD[d];
+    return (const T *)(c->layout ? c->phiT : c->phi);
+}
+
 template <class T> int op_fluid(fish_ctx *c, int d, bool fuse_cfl)
 {
     const T *in[8];
@@ -240,7 +250,7 @@ template <class T> int op_fluid(fish_ctx *c, int d, bool fuse_cfl)
     }
     for (int f = 0; f < 3; ++f) in[5 + f] = (const T *)c->bf[c->cb][f];
     FISH_CK(c,
-            Launch<T>::fluid(in, out, c->has_phi ? (const T *)(c->layout ? c->phiT : c->phi) : nullptr, c->dt_dev,
+            Launch<T>::fluid(in, out, sweep_potential<T>(c, d), c->dt_dev,
                              geom(c), d, c->lim, c->hse != 0, c->gamma, c->alpha, c->h, c->flags,
                              fuse_cfl ? c->minbits : nullptr, c->stream),
             "fluid sweep launch");
@@ -517,37 +527,56 @@ int fish_set_potential(fish_ctx *c, const double *phi)
         c->has_phi = false;
         return FISH_OK;
     }
-    if (!c->phi && !(c->phi = dev_alloc(c, (size_t)c->N * esize(c))))
-        return fail(c, FISH_ERR_OOM, "potential allocation failed");
-    if (!c->phiT && !(c->phiT = dev_alloc(c, (size_t)c->N * esize(c))))
-        return fail(c, FISH_ERR_OOM, "potential allocation failed");
     if (c->prec == FISH_PREC_FP64) {
+        if (!c->phi && !(c->phi = dev_alloc(c, (size_t)c->N * sizeof(double))))
+            return fail(c, FISH_ERR_OOM, "potential allocation failed");
+        if (!c->phiT && !(c->phiT = dev_alloc(c, (size_t)c->N * sizeof(double))))
+            return fail(c, FISH_ERR_OOM, "potential allocation failed");
         FISH_CK(c, cudaMemcpyAsync(c->phi, phi, c->N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "phi");
-    } else {
-        if ((r = ensure_stage(c))) return r;
-        for (long long o = 0; o < c->N; o += kStageChunk) {
-            const long long m = c->N - o < kStageChunk ? c->N - o : kStageChunk;
-            FISH_CK(c, cudaMemcpyAsync(c->stage, phi + o, m * sizeof(double), cudaMemcpyHostToDevice, c->stream),
-                    "phi");
-            FISH_CK(c, Launch<float>::from_f64(c->stage, (float *)c->phi + o, m, c->stream), "convert");
-            c->launches += 1;
-        }
-    }
-    {
         // the x sweeps read the potential in the y-fastest layout
         const void *src[8] = {c->phi};
         void *dst[8] = {c->phiT};
-        if (c->prec == FISH_PREC_FP64)
-            FISH_CK(c, Launch<double>::transpose((const double *const *)src, (double *const *)dst, 1, c->n[0], c->n[1],
-                                                 c->n[2], c->stream),
-                    "phi transpose");
-        else
-            FISH_CK(c, Launch<float>::transpose((const float *const *)src, (float *const *)dst, 1, c->n[0], c->n[1],
-                                                c->n[2], c->stream),
-                    "phi transpose");
+        FISH_CK(c, Launch<double>::transpose((const double *const *)src, (double *const *)dst, 1, c->n[0], c->n[1],
+                                             c->n[2], c->stream),
+                "phi transpose");
         c->launches += 1;
+        FISH_CK(c, cudaStreamSynchronize(c->stream), "phi upload");
+        c->has_phi = true;
+        return FISH_OK;
     }
-    FISH_CK(c, cudaStreamSynchronize(c->stream), "phi upload");
+    // FP32: per axis the difference to the next cell (periodic wrap or the
+    // outflow copy of the boundary cell), formed in FP64 and rounded once, so
+    // the hydrostatic estimate and the gravity source see no cancellation of
+    // the stored potential; the x differences in the y-fastest layout
+    for (int d = 0; d < 3; ++d)
+        if (!c->phiD[d] && !(c->phiD[d] = dev_alloc(c, (size_t)c->N * sizeof(float))))
+            return fail(c, FISH_ERR_OOM, "potential allocation failed");
+    const int nx = c->n[0], ny = c->n[1], nz = c->n[2];
+    const long long plane = (long long)nx * ny;
+    std::vector<float> dx(plane), dy(plane), dz(plane);
+    auto wrap = [&](int s, int n) { return c->bc == FISH_BC_PERIODIC ? (s >= n ? s - n : s) : (s >= n ? n - 1 : s); };
+    for (int k = 0; k < nz; ++k) {
+        const double *p0 = phi + (long long)k * plane;
+        const double *p1 = phi + (long long)wrap(k + 1, nz) * plane;
+        for (int j = 0; j < ny; ++j) {
+            const int jp = wrap(j + 1, ny);
+            for (int i = 0; i < nx; ++i) {
+                const int ip = wrap(i + 1, nx);
+                const double v = p0[(long long)j * nx + i];
+                dx[(long long)i * ny + j] = (float)(p0[(long long)j * nx + ip] - v);
+                dy[(long long)j * nx + i] = (float)(p0[(long long)jp * nx + i] - v);
+                dz[(long long)j * nx + i] = (float)(p1[(long long)j * nx + i] - v);
+            }
+        }
+        const long long off = (long long)k * plane;
+        FISH_CK(c, cudaMemcpyAsync((float *)c->phiD[0] + off, dx.data(), plane * sizeof(float), cudaMemcpyHostToDevice,
+                                   c->stream), "phi");
+        FISH_CK(c, cudaMemcpyAsync((float *)c->phiD[1] + off, dy.data(), plane * sizeof(float), cudaMemcpyHostToDevice,
+                                   c->stream), "phi");
+        FISH_CK(c, cudaMemcpyAsync((float *)c->phiD[2] + off, dz.data(), plane * sizeof(float), cudaMemcpyHostToDevice,
+                                   c->stream), "phi");
+        FISH_CK(c, cudaStreamSynchronize(c->stream), "phi upload");
+    }
     c->has_phi = true;
     return FISH_OK;
 }

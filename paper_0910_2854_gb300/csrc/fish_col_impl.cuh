@@ -82,12 +82,12 @@ template <class V> cudaError_t col_ct(const ColCTArgs<typename VT<V>::S> &A, boo
 {
     if constexpr (VT<V>::F64) {
         return ft1 ? col_ct_launch<V, -1, true>(A, s) : col_ct_launch<V, -1, false>(A, s);
-    } else if constexpr (std::is_same<V, P2>::value) {
+    } else {
+        // FP32: compile-time limiters for the throughput path
         if (A.lim == LIM_VANLEER) return col_ct_launch<V, LIM_VANLEER, true>(A, s);
         if (A.lim == LIM_MINMOD) return col_ct_launch<V, LIM_MINMOD, true>(A, s);
-        return cudaErrorInvalidValue;
-    } else {
-        return col_ct_launch<V, -1, true>(A, s);
+        if constexpr (std::is_same<V, P2>::value) return cudaErrorInvalidValue;
+        else return col_ct_launch<V, -1, true>(A, s);
     }
 }
 

@@ -33,7 +33,7 @@ template <class S> struct ColFluidArgs {
     const S *u[5];          // rho, m_d, m_t1, m_t2, E of the current buffer (sweep frame)
     const S *bd, *bt1, *bt2;  // face fields b_d, b_t1, b_t2 (sweep frame)
     S *uo[5];               // outputs, sweep frame
-    const S *phi;           // potential or nullptr
+    const S *phi;           // potential or nullptr; FP32: phi(next cell along d) - phi(cell), from FP64
     const double *dt;
     long long sd, so;       // strides along the sweep and the other transverse axis
     int n, nf, no;          // cells along the sweep, the fast and the other axis
@@ -182,7 +182,20 @@ __device__ __forceinline__ void ceval(const V u[5], const V bb[3], V gamma, V gm
     k.nsum = k.nsum + c.cf;
 }
 
-// hydrostatic estimate g (eq0321) and the HSE-corrected difference (eq0323)
+// Potential difference phi_b - phi_a across the interface a|b.  FP64 takes
+// the difference of the cell potentials; the FP32 kernels read, per cell,
+// the difference to the next cell along the sweep (formed in FP64 when the
+// potential is set), so phia already holds phi_b - phi_a.
+template <class V> __device__ __forceinline__ V pdiff(V phia, V phib)
+{
+    if constexpr (VT<V>::F64) return phib - phia;
+    else return phia;
+}
+
+// hydrostatic estimate g (eq0321) and the HSE-corrected difference (eq0323).
+// FP32 island: g = s * fac is split into its rounded value and the exact
+// rounding error (TwoProduct with an FMA), both subtracted from du, so the
+// cancellation du - g near equilibrium adds no product rounding.
 template <class V>
 __device__ __forceinline__ void chse(const CCell<V> &a, const CCell<V> &b, V phia, V phib, V du[5], V ddu[5])
 {
@@ -194,12 +207,19 @@ __device__ __forceinline__ void chse(const CCell<V> &a, const CCell<V> &b, V phi
     }
     xa[4] = -(a.u[4] + a.p);
     xb[4] = -(b.u[4] + b.p);
-    const V fac = vdiv(phib - phia, a.cs * b.cs);
+    const V fac = vdiv(pdiff(phia, phib), a.cs * b.cs);
 #pragma unroll
     for (int i = 0; i < 5; ++i) {
-        const V g = vb<V>(0.5f) * (xb[i] + xa[i]) * fac;
         du[i] = b.u[i] - a.u[i];
-        ddu[i] = vminmod(du[i] - g, du[i]);
+        if constexpr (VT<V>::F64) {
+            const V g = 0.5 * (xb[i] + xa[i]) * fac;
+            ddu[i] = vminmod(du[i] - g, du[i]);
+        } else {
+            const V sx = vb<V>(0.5f) * (xb[i] + xa[i]);
+            const V ghi = sx * fac;
+            const V glo = vfma(sx, fac, -ghi);
+            ddu[i] = vminmod((du[i] - ghi) - glo, du[i]);
+        }
     }
 }
 
@@ -366,7 +386,13 @@ __device__ __forceinline__ void fload_mapped(const ColFluidArgs<typename VT<V>::
     R.bfm = __ldg(bfp + i + X.ofm);
     R.bo = vload<V>(bop, i);
     R.bom = vload<V>(bop, i + X.oom);
-    if (GRAV) R.phi = vload<V>(A.phi, i);
+    if (GRAV) {
+        // FP32 reads the difference to the next cell: zero between the copies
+        // of an outflow boundary cell (and across its face)
+        R.phi = vload<V>(A.phi, i);
+        if constexpr (!VT<V>::F64)
+            if (A.bc == BC_OUTFLOW && (s < 0 || s >= A.n)) R.phi = vb<V>(0.0f);
+    }
 }
 
 // load interior cell at element offset i (no map; its lower b_d face is the
@@ -476,9 +502,10 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
             else up[k] = vfma(-lamh, M.F1[k2][k] - M.F1[p2][k], cp.u[k]);
         }
         if (GRAV) {
+            // centred difference phi_r - phi_{r-2} (eq02513)
             V dphi;
             if constexpr (VT<V>::F64) dphi = (phr - M.phm2) / (2.0 * A.h);
-            else dphi = (phr - M.phm2) * rtwoh;
+            else dphi = (M.ph[p2] + M.phm2) * rtwoh;
             up[1] = up[1] - hdt * cp.u[0] * dphi;
             up[4] = up[4] - hdt * cp.u[1] * dphi;
         }
@@ -500,7 +527,7 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
                     // corrector source from the predicted state (eq0255)
                     V dphi;
                     if constexpr (VT<V>::F64) dphi = (M.q[s2] - M.q[s0]) / (2.0 * A.h);
-                    else dphi = (M.q[s2] - M.q[s0]) * rtwoh;
+                    else dphi = (M.q[s0] + M.q[s1]) * rtwoh;
                     un[1] = un[1] - dt * M.P[s1].u[0] * dphi;
                     un[4] = un[4] - dt * M.P[s1].u[1] * dphi;
                 }
@@ -841,7 +868,7 @@ __device__ __forceinline__ void ctstep(const ColCTArgs<typename VT<V>::S> &A, co
 }
 
 #ifndef FISH_CT_MINB
-#define FISH_CT_MINB 3
+#define FISH_CT_MINB 4
 #endif
 
 // B_d over all columns (eq0350 advection of the transverse components,
