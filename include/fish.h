@@ -156,6 +156,50 @@ const char *fish_last_error(fish_ctx *ctx);
 /* Number of kernel launches queued by this context since creation. */
 long long fish_launch_count(fish_ctx *ctx);
 
+/* ---- batches of independent boxes (FP32) ---------------------------------
+ * Many boxes of uneven sizes advanced together: every sweep of every box is
+ * one persistent launch over a device work queue, each box keeps its own CFL
+ * time step on the device, and the double step of the whole batch is one
+ * CUDA graph.  Each box follows exactly the single-box FP32 path (eq0081-
+ * eq0084 with the operators of Sec. 2): its result equals that of a fish_ctx
+ * of the same box stepped with fish_step_cfl.  The state layout of a box is
+ * the one above.  Every box needs even nx and ny (the x and y columns are
+ * advanced in pairs). */
+typedef struct fish_batch fish_batch;
+
+/* batch option keys (fish_batch_set_option) */
+enum {
+    FISH_BATCH_OPT_LIMITER = 0, /* FISH_LIM_VANLEER (default) or FISH_LIM_MINMOD */
+    FISH_BATCH_OPT_ORDER = 1,   /* work-item order: 0 box order, 1 longest first, 2 round robin */
+    FISH_BATCH_OPT_GROUPS = 2,  /* column groups (128 threads) per work item: 1, 2, 4, 8 */
+    FISH_BATCH_OPT_GRID = 3     /* persistent grid = SMs x resident blocks x (1, 2 or 4) */
+};
+
+/* nbox boxes: dims[3k..3k+2] = nx, ny, nz of box k, gamma[k] > 1, bc[k]
+ * FISH_BC_*, h[3k..3k+2] cell widths (NULL: 1/n per axis).  Allocates the
+ * device memory of all boxes (two buffers of 8 FP32 fields). */
+int fish_batch_create(int nbox, const int *dims, const double *gamma, const int *bc, const double *h,
+                      fish_batch **out);
+int fish_batch_set_option(fish_batch *b, int key, double value);
+/* queue all further work on this CUDA stream (NULL: the batch's own) */
+int fish_batch_set_stream(fish_batch *b, void *cuda_stream);
+/* upload box `box` from a host buffer of 8*nx*ny*nz doubles; synchronous */
+int fish_batch_set_state(fish_batch *b, int box, const double *state);
+/* nsteps double steps of every box, each with dt = k * CFL of that box's
+ * state at the start of the step, computed on the device.  Asynchronous. */
+int fish_batch_step(fish_batch *b, double k, int nsteps);
+/* download box `box` into a host buffer of 8*nx*ny*nz doubles; synchronises
+ * and returns FISH_ERR_NONPHYSICAL if any box met rho <= 0, p <= 0 or NaN */
+int fish_batch_get_state(fish_batch *b, int box, double *state);
+/* dt of the last step of every box into dt[nbox]; synchronises */
+int fish_batch_last_dt(fish_batch *b, double *dt);
+int fish_batch_sync(fish_batch *b);
+const char *fish_batch_last_error(fish_batch *b);
+long long fish_batch_launch_count(fish_batch *b);
+/* total cells of all boxes */
+long long fish_batch_cells(fish_batch *b);
+void fish_batch_destroy(fish_batch *b);
+
 /* Allocation-free diagnostics of a device-resident state.  The paper has no
  * counterpart: this call serves callers that cannot let a library allocate
  * device memory -- host codes that own all device memory through their own

@@ -26,13 +26,17 @@ FISH_PREC_FP64, FISH_PREC_FP32 = 0, 1
 FISH_LIM_VANLEER, FISH_LIM_MINMOD, FISH_LIM_NONE = 0, 1, 2
 FISH_F64, FISH_F32 = 0, 1
 FISH_OP_FLUID, FISH_OP_CT = 0, 1
+FISH_BATCH_OPT_LIMITER, FISH_BATCH_OPT_ORDER, FISH_BATCH_OPT_GROUPS, FISH_BATCH_OPT_GRID = range(4)
 
 # every symbol include/fish.h declares (checked by the CPU test suite)
 EXPORTS = ("fish_create", "fish_set_option", "fish_set_stream", "fish_set_allocator", "fish_set_state",
            "fish_set_state_device", "fish_set_state_host", "fish_set_potential", "fish_cfl_dt", "fish_step", "fish_step_cfl",
            "fish_last_dt", "fish_apply", "fish_get_state", "fish_get_state_device", "fish_diagnostics",
            "fish_sync", "fish_clear_error", "fish_last_error", "fish_launch_count", "fish_destroy",
-           "fish_diagnostics_noalloc")
+           "fish_diagnostics_noalloc", "fish_batch_create", "fish_batch_set_option", "fish_batch_set_stream",
+           "fish_batch_set_state", "fish_batch_step", "fish_batch_get_state", "fish_batch_last_dt",
+           "fish_batch_sync", "fish_batch_last_error", "fish_batch_launch_count", "fish_batch_cells",
+           "fish_batch_destroy")
 
 _ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -83,6 +87,19 @@ def load(path: str = LIB_PATH):
             "fish_destroy": ([P], None),
             "fish_diagnostics_noalloc": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P], ctypes.c_int),
+            "fish_batch_create": ([ctypes.c_int, ctypes.POINTER(ctypes.c_int), D, ctypes.POINTER(ctypes.c_int), D,
+                                   ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+            "fish_batch_set_option": ([P, ctypes.c_int, ctypes.c_double], ctypes.c_int),
+            "fish_batch_set_stream": ([P, P], ctypes.c_int),
+            "fish_batch_set_state": ([P, ctypes.c_int, D], ctypes.c_int),
+            "fish_batch_step": ([P, ctypes.c_double, ctypes.c_int], ctypes.c_int),
+            "fish_batch_get_state": ([P, ctypes.c_int, D], ctypes.c_int),
+            "fish_batch_last_dt": ([P, D], ctypes.c_int),
+            "fish_batch_sync": ([P], ctypes.c_int),
+            "fish_batch_last_error": ([P], ctypes.c_char_p),
+            "fish_batch_launch_count": ([P], ctypes.c_longlong),
+            "fish_batch_cells": ([P], ctypes.c_longlong),
+            "fish_batch_destroy": ([P], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -309,3 +326,90 @@ def diagnostics_noalloc(state, dims, bc, h, out, stream=None):
     if code != FISH_OK:
         raise FishError(code, "fish_diagnostics_noalloc failed")
     return out
+
+
+class Batch:
+    """Many independent FP32 boxes of uneven sizes advanced together (wraps
+    a fish_batch).  ``dims``: list of (nx, ny, nz) (nx, ny even); ``gammas``,
+    ``bcs``: per box; ``hs``: per-box cell widths or None (1/n)."""
+
+    def __init__(self, dims, gammas, bcs, hs=None, limiter=FISH_LIM_VANLEER, stream=None):
+        self._lib = load()
+        self.dims = [tuple(int(v) for v in d) for d in dims]
+        n = len(self.dims)
+        d = (ctypes.c_int * (3 * n))(*[v for t in self.dims for v in t])
+        g = (ctypes.c_double * n)(*[float(x) for x in gammas])
+        b = (ctypes.c_int * n)(*[int(x) for x in bcs])
+        h = None if hs is None else (ctypes.c_double * (3 * n))(*[float(v) for t in hs for v in t])
+        out = ctypes.c_void_p()
+        code = self._lib.fish_batch_create(n, d, g, b, h, ctypes.byref(out))
+        if code != FISH_OK:
+            raise FishError(code, "fish_batch_create failed")
+        self.ptr = out
+        self._stream = None
+        try:
+            self.set_option(FISH_BATCH_OPT_LIMITER, limiter)
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    self._stream = stream if stream is not None else torch.cuda.Stream()
+                    self._check(self._lib.fish_batch_set_stream(self.ptr, ctypes.c_void_p(self._stream.cuda_stream)),
+                                "fish_batch_set_stream")
+            except ImportError:
+                pass
+        except Exception:
+            self.close()
+            raise
+
+    @property
+    def stream(self):
+        return self._stream
+
+    def _check(self, code, what):
+        if code != FISH_OK:
+            msg = self._lib.fish_batch_last_error(self.ptr).decode(errors="replace") if self.ptr else ""
+            raise FishError(code, "%s failed: %s" % (what, msg))
+
+    def set_option(self, key, value):
+        self._check(self._lib.fish_batch_set_option(self.ptr, int(key), float(value)), "fish_batch_set_option")
+
+    def set_state(self, box, state):
+        a = np.ascontiguousarray(state, dtype=np.float64)
+        if a.size != 8 * int(np.prod(self.dims[box])):
+            raise ValueError("state of box %d has the wrong size" % box)
+        self._check(self._lib.fish_batch_set_state(self.ptr, int(box), _dptr(a)), "fish_batch_set_state")
+
+    def step(self, k, nsteps=1):
+        self._check(self._lib.fish_batch_step(self.ptr, float(k), int(nsteps)), "fish_batch_step")
+
+    def get_state(self, box):
+        nx, ny, nz = self.dims[box]
+        out = np.empty((8, nz, ny, nx), dtype=np.float64)
+        self._check(self._lib.fish_batch_get_state(self.ptr, int(box), _dptr(out)), "fish_batch_get_state")
+        return out
+
+    def last_dt(self):
+        out = np.zeros(len(self.dims), dtype=np.float64)
+        self._check(self._lib.fish_batch_last_dt(self.ptr, _dptr(out)), "fish_batch_last_dt")
+        return out
+
+    def sync(self):
+        self._check(self._lib.fish_batch_sync(self.ptr), "fish_batch_sync")
+
+    @property
+    def cells(self):
+        return int(self._lib.fish_batch_cells(self.ptr))
+
+    def launch_count(self):
+        return int(self._lib.fish_batch_launch_count(self.ptr))
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            self._lib.fish_batch_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

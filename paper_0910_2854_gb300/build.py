@@ -6,6 +6,7 @@ Three translation units compiled in parallel, then linked:
   fish_p2.cu   -- FP32 two-column sweep kernels (packed FP32x2)
   fish_capi.cu -- host-side C ABI
   fish_noalloc.cu -- the allocation-free diagnostics entry point
+  fish_batch.cu -- batches of independent boxes (FP32)
 """
 from __future__ import annotations
 
@@ -27,6 +28,7 @@ UNITS = {
     "fish_p2.cu": ["-prec-sqrt=false", "-ftz=true"],
     "fish_capi.cu": [],
     "fish_noalloc.cu": [],
+    "fish_batch.cu": ["-prec-sqrt=false", "-ftz=true"],
 }
 
 

@@ -35,6 +35,7 @@ template <class S> struct ColFluidArgs {
     S *uo[5];               // outputs, sweep frame
     const S *phi;           // potential or nullptr; FP32: phi(next cell along d) - phi(cell), from FP64
     const double *dt;
+    long long off;          // element offset of the box in the field arrays (batches; else 0)
     long long sd, so;       // strides along the sweep and the other transverse axis
     int n, nf, no;          // cells along the sweep, the fast and the other axis
     int bc;
@@ -55,6 +56,7 @@ template <class S> struct ColCTArgs {
     const S *bd, *bf, *bo;  // b_d and the face fields of the fast and other transverse axes
     S *bdo, *bfo, *boo;     // outputs (other buffer)
     const double *dt;
+    long long off;          // element offset of the box in the field arrays (batches; else 0)
     long long sd, so;
     int n, nf, no;
     int bc;
@@ -582,19 +584,18 @@ __device__ __forceinline__ void fprologue(const ColFluidArgs<typename VT<V>::S> 
 #define FISH_COL_MINB1 3   // one-column FP32 kernels
 #endif
 
-template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool CFLF = false>
-__global__ void __launch_bounds__(128, VT<V>::F64 ? 1 : (VT<V>::W == 2 || HSE ? FISH_COL_MINB : FISH_COL_MINB1))
-    fluid_col_kernel(const ColFluidArgs<typename VT<V>::S> A)
+// The march of thread cid (column group cid of the box described by A).
+template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool CFLF>
+__device__ __forceinline__ void fluid_columns(const ColFluidArgs<typename VT<V>::S> &A, long long cid)
 {
     using S = typename VT<V>::S;
     constexpr int W = VT<V>::W;
     const int cols = A.nf / W;
-    const long long cid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (cid >= (long long)cols * A.no) return;
     const int fp = (int)(cid % cols), ob = (int)(cid / cols);
     const int f0 = fp * W;
     FCtx<S> X;
-    X.base = (long long)f0 + (long long)ob * A.so;
+    X.base = A.off + (long long)f0 + (long long)ob * A.so;
     X.ofm = (long long)(gmap(f0 - 1, A.nf, A.bc) - f0);
     X.oom = (long long)(gmap(ob - 1, A.no, A.bc) - ob) * A.so;
     const double dtd = *A.dt;
@@ -654,6 +655,13 @@ __global__ void __launch_bounds__(128, VT<V>::F64 ? 1 : (VT<V>::W == 2 || HSE ? 
             }
         }
     }
+}
+
+template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool CFLF = false>
+__global__ void __launch_bounds__(128, VT<V>::F64 ? 1 : (VT<V>::W == 2 || HSE ? FISH_COL_MINB : FISH_COL_MINB1))
+    fluid_col_kernel(const ColFluidArgs<typename VT<V>::S> A)
+{
+    fluid_columns<V, HSE, GRAV, LIM, FT1, CFLF>(A, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -875,14 +883,13 @@ __device__ __forceinline__ void ctstep(const ColCTArgs<typename VT<V>::S> &A, co
 // eq0360 constraint update of b_d from the same edge fluxes).  Every lane of
 // a warp takes the same steps (shuffles); lanes without columns of their
 // own repeat a valid column and store nothing.
+// The march of warp gw (31 W columns of one row) of the box described by A.
 template <class V, int LIM, bool FT1>
-__global__ void __launch_bounds__(128, VT<V>::F64 ? 1 : FISH_CT_MINB) ct_col_kernel(const ColCTArgs<typename VT<V>::S> A)
+__device__ __forceinline__ void ct_columns(const ColCTArgs<typename VT<V>::S> &A, long long gw, int lane)
 {
     using S = typename VT<V>::S;
     constexpr int W = VT<V>::W;
     constexpr int SEGC = 31 * W;  // output columns per warp
-    const int lane = threadIdx.x & 31;
-    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nseg = (A.nf + SEGC - 1) / SEGC;
     if (gw >= (long long)nseg * A.no) return;  // whole warps only
     const int seg = (int)(gw % nseg), ob = (int)(gw / nseg);
@@ -901,7 +908,7 @@ __global__ void __launch_bounds__(128, VT<V>::F64 ? 1 : FISH_CT_MINB) ct_col_ker
         X.fixy = W == 2;
     }
     const int cfp = gmap(cl + W, A.nf, A.bc);
-    X.base = (long long)cb + (long long)ob * A.so;
+    X.base = A.off + (long long)cb + (long long)ob * A.so;
     X.ofp = (long long)(cfp - cb);
     X.oom = (long long)(gmap(ob - 1, A.no, A.bc) - ob) * A.so;
     X.oop = (long long)(gmap(ob + 1, A.no, A.bc) - ob) * A.so;
@@ -958,6 +965,12 @@ __global__ void __launch_bounds__(128, VT<V>::F64 ? 1 : FISH_CT_MINB) ct_col_ker
     if (s + 5 <= n + 3) ctstep<V, LIM, FT1, 1, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 5, lamh, lam, lamf, lamo);
     if (s + 6 <= n + 3) ctstep<V, LIM, FT1, 2, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 6, lamh, lam, lamf, lamo);
     if (s + 7 <= n + 3) ctstep<V, LIM, FT1, 3, true, true, true, true, CL_NONE, false>(A, X, M, s + 7, lamh, lam, lamf, lamo);
+}
+
+template <class V, int LIM, bool FT1>
+__global__ void __launch_bounds__(128, VT<V>::F64 ? 1 : FISH_CT_MINB) ct_col_kernel(const ColCTArgs<typename VT<V>::S> A)
+{
+    ct_columns<V, LIM, FT1>(A, ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------

@@ -83,6 +83,7 @@ cudaError_t Launch<T>::fluid(const T *const in[8], T *const out[5], const T *phi
     A.bt2 = in[5 + a2];
     A.phi = phi;
     A.dt = dt;
+    A.off = 0;
     A.sd = F.sd;
     A.so = F.so;
     A.n = F.n;
@@ -126,6 +127,7 @@ cudaError_t Launch<T>::ct(const T *rho, const T *md, const T *const b[3], T *con
     A.bfo = bout[F.fast];
     A.boo = bout[F.other];
     A.dt = dt;
+    A.off = 0;
     A.sd = F.sd;
     A.so = F.so;
     A.n = F.n;

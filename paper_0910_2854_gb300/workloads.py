@@ -336,15 +336,17 @@ def random_smooth(nx, ny, nz, seed=0, gamma=5.0 / 3.0, vamp=0.3, bamp=0.1, bmean
 
 
 def blast(nx, ny, nz, gamma=5.0 / 3.0, p_in=100.0, p_out=1.0, b=(1.0, 0.0, 0.0), radius_frac=0.1,
-          bc=BC_PERIODIC):
+          bc=BC_PERIODIC, centre=(0.5, 0.5, 0.5)):
     """Spherical blast: rho = 1, v = 0, p = p_in inside r < radius_frac times
-    the shortest box side (centred), p_out outside, uniform b, unit cells
-    scaled so the longest side has length 1."""
+    the shortest box side, p_out outside, uniform b, unit cells scaled so the
+    longest side has length 1.  ``centre``: position of the centre as a
+    fraction of each side (the default centres the blast, which makes the
+    flow mirror-symmetric about the box's mid-planes)."""
     L = float(max(nx, ny, nz))
     h = 1.0 / L
-    xs = (np.arange(nx) + 0.5) * h - 0.5 * nx * h
-    ys = (np.arange(ny) + 0.5) * h - 0.5 * ny * h
-    zs = (np.arange(nz) + 0.5) * h - 0.5 * nz * h
+    xs = (np.arange(nx) + 0.5) * h - centre[0] * nx * h
+    ys = (np.arange(ny) + 0.5) * h - centre[1] * ny * h
+    zs = (np.arange(nz) + 0.5) * h - centre[2] * nz * h
     Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
     r = np.sqrt(X * X + Y * Y + Z * Z)
     R = radius_frac * min(nx, ny, nz) * h
