@@ -65,6 +65,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batch", action="store_true")
     return p.parse_args()
 
 
@@ -234,15 +235,15 @@ def time_operators(F, box, torch, reps=3):
     return out
 
 
+# DRAM bytes per cell of one launch of each kernel kind, from the ncu
+# capture summarised in profiles/sweeps_f32_turbulence_384.md (384^3 launch,
+# dram__bytes_read.sum + dram__bytes_write.sum over its cells).  Set an entry
+# to None when that kernel changes until it is captured again.
+TRAFFIC_B_PER_CELL = {"fluid": 52.2, "ct": 31.95}
+
+
 def traffic_per_cell(kernel_key):
-    """DRAM bytes per cell of one launch from the committed ncu summary, if
-    taken on the current kernels (profiles/traffic.json), else None."""
-    try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            t = json.load(f)
-        return t.get(kernel_key)
-    except Exception:
-        return None
+    return TRAFFIC_B_PER_CELL.get(kernel_key.split("_")[0])
 
 
 def e2e_rate(F, box, torch, n, steps):
@@ -332,6 +333,15 @@ def run_fish(args, rank, world, local):
             fp64 = {"workload": FP64_WORKLOAD["workload"], "value": v64, "unit": UNIT, "ms_per_step": ms64 / k64,
                     "fp32_over_fp64": (value / world) / v64}
             b64.close()
+        batch = None
+        if not args.no_batch:
+            from paper_0910_2854_gb300 import reports
+            try:
+                batch = reports.batch()
+                batch["workload"] = ("batch of 64 seeded boxes 32^3..160^3 (Sod / Brio-Wu / blast), FP32, one graph "
+                                     "of persistent work-queue sweeps per double step, autotuned")
+            except Exception as exc:  # report, do not hide
+                batch = {"error": repr(exc)[:200]}
         cpu = None
         if not args.no_cpu_baseline:
             rate, steps, el, cores, cells = oracle_rate(128, budget_s=10.0)
@@ -346,7 +356,7 @@ def run_fish(args, rank, world, local):
                              "l2": "inputs larger than L2 (34 GB state vs 129 MB L2)",
                              "graph": "one CUDA graph per double step (CFL + 12 sweeps)"},
                   "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-                  "clocks": clk, "fp64_path": fp64}
+                  "clocks": clk, "fp64_path": fp64, "batch": batch}
     else:
         box.close()
     if world > 1:
