@@ -291,13 +291,11 @@ def run_fish(args, rank, world, local):
     ms, launches = time_steps(box, torch, args.steps, args.warmup)
     barrier()
     clk = clocks.stop()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    # cells of all ranks over the slowest rank's time (every rank its own box)
+    from paper_0910_2854_gb300.replicas import job_throughput
+    rate, ms = job_throughput(ms, n ** 3 * args.steps, device="cuda")
     ms_step = ms / args.steps
-    value = world * n ** 3 / (ms_step * 1e-3)
+    value = rate
 
     result = None
     if rank == 0:
