@@ -58,9 +58,11 @@ struct fish_ctx {
     double *partial = nullptr;
     double *stage = nullptr;        // conversion staging (kStageChunk doubles)
 
-    cudaGraphExec_t gexec = nullptr;
+    // one captured double step per starting buffer parity (cu*2 + cb): a step
+    // whose sweeps also change the layout ends on the other parity
+    cudaGraphExec_t gexec[4] = {};
+    int gend[4] = {0, 0, 0, 0};   // parity after the step
     double gk = -1.0;
-    int gparity = -1;
     bool gdirty = true;
     bool gfused = false;       // the graph's last sweep reduces the next CFL
     long long glaunches = 0;   // kernels per graph replay
@@ -604,6 +606,49 @@ int fish_step(fish_ctx *c, double dt)
     return queue_sweeps(c);
 }
 
+// Capture one double step starting from the current buffers (the host's
+// buffer bookkeeping is restored afterwards); the graph of parity p and the
+// parity it ends on.
+int capture_step(fish_ctx *c, double k, bool fused, int p)
+{
+    const int cu0 = c->cu, cb0 = c->cb, lay0 = c->layout;
+    const long long l0 = c->launches;
+    cudaStream_t cap = c->stream;
+    cudaGraph_t graph = nullptr;
+    FISH_CK(c, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    int r;
+    if (fused) {
+        cudaError_t e0 = fish::launch_cfl_finish(c->minbits, k, c->dt_dev, c->dt_last, cap);
+        r = e0 == cudaSuccess ? FISH_OK : cuda_fail(c, e0, "cfl finish launch");
+        c->launches += 1;
+    } else {
+        r = queue_cfl_dt(c, k, c->dt_dev, c->dt_last);
+    }
+    if (!r) r = queue_sweeps(c, fused);
+    cudaError_t e = cudaStreamEndCapture(cap, &graph);
+    const int pend = c->cu * 2 + c->cb;
+    const bool lay_ok = c->layout == lay0;
+    c->cu = cu0;
+    c->cb = cb0;
+    c->layout = lay0;
+    c->glaunches = c->launches - l0;
+    c->launches = l0;  // captured, not launched
+    if (r) {
+        if (graph) cudaGraphDestroy(graph);
+        return r;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+    if (!lay_ok) {
+        cudaGraphDestroy(graph);
+        return fail(c, FISH_ERR_STATE, "double step does not end in its starting layout");
+    }
+    e = cudaGraphInstantiate(&c->gexec[p], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+    c->gend[p] = pend;
+    return FISH_OK;
+}
+
 int fish_step_cfl(fish_ctx *c, double k, int nsteps)
 {
     int r = ready(c);
@@ -612,41 +657,14 @@ int fish_step_cfl(fish_ctx *c, double k, int nsteps)
     if (nsteps == 0) return FISH_OK;
     // every replay starts (and ends) in the layout of the x sweeps
     if ((r = set_layout(c, layout_for(0)))) return r;
-    const int parity = c->cu * 2 + c->cb;
     const bool fused = last_sweep_fuses_cfl(c);
-    if (c->gdirty || !c->gexec || c->gk != k || c->gparity != parity || c->gfused != fused) {
-        if (c->gexec) {
-            cudaGraphExecDestroy(c->gexec);
-            c->gexec = nullptr;
-        }
-        // capture one double step: dt from the CFL minimum (reduced by the
-        // previous replay's last sweep when fused, else by a CFL pass at the
-        // start), then the twelve operators
-        cudaStream_t cap = c->stream;
-        cudaGraph_t graph = nullptr;
-        const long long l0 = c->launches;
-        FISH_CK(c, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal), "begin capture");
-        if (fused) {
-            cudaError_t e0 = fish::launch_cfl_finish(c->minbits, k, c->dt_dev, c->dt_last, cap);
-            r = e0 == cudaSuccess ? FISH_OK : cuda_fail(c, e0, "cfl finish launch");
-            c->launches += 1;
-        } else {
-            r = queue_cfl_dt(c, k, c->dt_dev, c->dt_last);
-        }
-        if (!r) r = queue_sweeps(c, fused);
-        cudaError_t e = cudaStreamEndCapture(cap, &graph);
-        if (r) {
-            if (graph) cudaGraphDestroy(graph);
-            return r;
-        }
-        if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
-        e = cudaGraphInstantiate(&c->gexec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
-        c->glaunches = c->launches - l0;
-        c->launches = l0;  // captured, not launched
+    if (c->gdirty || c->gk != k || c->gfused != fused) {
+        for (auto &g : c->gexec)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
         c->gk = k;
-        c->gparity = parity;
         c->gfused = fused;
         c->gdirty = false;
     }
@@ -655,8 +673,12 @@ int fish_step_cfl(fish_ctx *c, double k, int nsteps)
         if ((r = queue_cfl_min(c))) return r;
     }
     for (int s = 0; s < nsteps; ++s) {
-        FISH_CK(c, cudaGraphLaunch(c->gexec, c->stream), "graph launch");
+        const int p = c->cu * 2 + c->cb;
+        if (!c->gexec[p] && (r = capture_step(c, k, fused, p))) return r;
+        FISH_CK(c, cudaGraphLaunch(c->gexec[p], c->stream), "graph launch");
         c->launches += c->glaunches;
+        c->cu = c->gend[p] >> 1;
+        c->cb = c->gend[p] & 1;
     }
     c->cfl_pending = fused;
     return FISH_OK;
@@ -796,7 +818,8 @@ void fish_destroy(fish_ctx *c)
 {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    for (auto g : c->gexec)
+        if (g) cudaGraphExecDestroy(g);
     dev_free_all(c);
     if (c->own) cudaStreamDestroy(c->own);
     delete c;
