@@ -20,6 +20,12 @@ Parity status of the functions (what pins each one; see ``tests/test_oracle_*``)
     the mass flux vanishes; the polytrope behaviour of the paper's Sec. 4 is
     not yet reproduced, so its second-order construction is partly unpinned.
   * ``cfl``: pinned by closed-form fast speeds on a uniform state.
+  * hybrid limiter (``limiter=LIM_HYBRID``): pinned by its two limits (a
+    subsonic flow gives the Van Leer result bitwise, a supersonic one the
+    minmod result) and a mixed flow that differs from both.
+  * operator-split gravity (``gravity_split=True``): pinned by the exact
+    impulse and kinetic-energy change of a uniform state in a linear
+    potential.
   * ``test_oracle_mutants.py`` plants mistakes in a copy of the source and
     checks that the pins catch each of them.
 """
@@ -37,7 +43,7 @@ _SRC = os.path.join(_HERE, "fish_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libfish_oracle.so")
 
-LIM_VANLEER, LIM_MINMOD, LIM_NONE = 0, 1, 2
+LIM_VANLEER, LIM_MINMOD, LIM_NONE, LIM_HYBRID = 0, 1, 2, 3
 BC_PERIODIC, BC_OUTFLOW = 0, 1
 FIELDS = ("rho", "mx", "my", "mz", "E", "bx", "by", "bz")
 
@@ -82,7 +88,8 @@ class _Problem(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("bc", ctypes.c_int),
                 ("limiter", ctypes.c_int), ("hse", ctypes.c_int),
                 ("pred_diss", ctypes.c_double),
-                ("phi", ctypes.POINTER(ctypes.c_double))]
+                ("phi", ctypes.POINTER(ctypes.c_double)),
+                ("gravity_split", ctypes.c_int)]
 
 
 def _bind(lib):
@@ -126,7 +133,7 @@ class OracleBox:
     """
 
     def __init__(self, nx, ny, nz, gamma, bc=BC_PERIODIC, h=None,
-                 limiter=LIM_VANLEER, hse=False, pred_diss=1.0, phi=None, lib=None):
+                 limiter=LIM_VANLEER, hse=False, pred_diss=1.0, phi=None, gravity_split=False, lib=None):
         self._lib = lib
         self.n = (int(nx), int(ny), int(nz))
         if h is None:
@@ -137,6 +144,7 @@ class OracleBox:
         self.limiter = int(limiter)
         self.hse = bool(hse)
         self.pred_diss = float(pred_diss)
+        self.gravity_split = bool(gravity_split)
         self.state = np.zeros((8, nz, ny, nx), dtype=np.float64)
         self.phi = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64).reshape(nz, ny, nx)
         self.flags = 0
@@ -154,6 +162,7 @@ class OracleBox:
         p.limiter = self.limiter
         p.hse = 1 if self.hse else 0
         p.pred_diss = self.pred_diss
+        p.gravity_split = 1 if self.gravity_split else 0
         if self.phi is not None:
             p.phi = self.phi.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         else:

@@ -38,7 +38,7 @@
 
 #define OR_NG 4 /* ghost cells gathered at each pencil end */
 
-enum { OR_LIM_VANLEER = 0, OR_LIM_MINMOD = 1, OR_LIM_NONE = 2 };
+enum { OR_LIM_VANLEER = 0, OR_LIM_MINMOD = 1, OR_LIM_NONE = 2, OR_LIM_HYBRID = 3 };
 enum { OR_BC_PERIODIC = 0, OR_BC_OUTFLOW = 1 };
 enum { OR_FLAG_RHO = 1, OR_FLAG_P = 2, OR_FLAG_NAN = 4 };
 
@@ -52,6 +52,7 @@ typedef struct {
     int hse;             /* 1: hydrostatic-gradient correction (eq0321-eq03261) */
     double pred_diss;    /* predictor freezing-speed factor in [0,1] (Sec. 2.2, predictor step) */
     const double *phi;   /* NULL or cell-centred potential, nx*ny*nz */
+    int gravity_split;   /* 1: operator-split gravity G(dt/2) L G(dt/2) (eq025111-eq02513) */
 } or_problem;
 
 /* ------------------------------------------------------------------------ */
@@ -242,6 +243,12 @@ static void or_flux2(const or_problem *P, const or_cell *c0, const or_cell *c1,
                      const or_cell *c2, const or_cell *c3, const double ph[4], double F[5])
 {
     int k;
+    /* hybrid limiter (Sec. 2.2, after eq0200): Van Leer where the flow is
+     * subsonic, minmod where it is supersonic; decided per interface from the
+     * two cells that share it (reading C-21) */
+    int lim = P->limiter;
+    if (lim == OR_LIM_HYBRID)
+        lim = (fabs(c1->vn) > c1->cs || fabs(c2->vn) > c2->cs) ? OR_LIM_MINMOD : OR_LIM_VANLEER;
     if (!P->hse) {
         double D = fmax(c1->d, c2->d);
         for (k = 0; k < 5; ++k) {
@@ -251,8 +258,8 @@ static void or_flux2(const or_problem *P, const or_cell *c0, const or_cell *c1,
             double fm1 = 0.5 * (c1->F[k] - D * c1->u[k]);
             double fm2 = 0.5 * (c2->F[k] - D * c2->u[k]);
             double fm3 = 0.5 * (c3->F[k] - D * c3->u[k]);
-            double slp = or_limit(P->limiter, fp1 - fp0, fp2 - fp1);   /* eq0180 */
-            double slm = or_limit(P->limiter, fm2 - fm1, fm3 - fm2);   /* eq0220 */
+            double slp = or_limit(lim, fp1 - fp0, fp2 - fp1);   /* eq0180 */
+            double slm = or_limit(lim, fm2 - fm1, fm3 - fm2);   /* eq0220 */
             F[k] = fp1 + fm2 + 0.5 * (slp - slm);                      /* eq0230 */
         }
     } else {
@@ -270,8 +277,8 @@ static void or_flux2(const or_problem *P, const or_cell *c0, const or_cell *c1,
             double fp_r = 0.5 * ((c2->F[k] - c1->F[k]) + q1);  /* F+_{e+1} - F+_e    */
             double fm_l = 0.5 * ((c2->F[k] - c1->F[k]) - q1);  /* F-_{e+1} - F-_e    */
             double fm_r = 0.5 * ((c3->F[k] - c2->F[k]) - q2);  /* F-_{e+2} - F-_{e+1} */
-            double slp = or_limit(P->limiter, fp_l, fp_r);
-            double slm = or_limit(P->limiter, fm_l, fm_r);
+            double slp = or_limit(lim, fp_l, fp_r);
+            double slm = or_limit(lim, fm_l, fm_r);
             F[k] = 0.5 * (c1->F[k] + c2->F[k]) - 0.5 * q1 + 0.5 * (slp - slm);
         }
     }
@@ -335,7 +342,7 @@ static int or_fluid_pencil(const or_problem *P, double *const *q, int d, long a,
     const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
     const double hd = P->h[d];
     const double alpha = P->pred_diss;
-    const int grav = P->phi != NULL;
+    const int grav = P->phi != NULL && !P->gravity_split;  /* unsplit source terms */
     int flags = 0;
     long e;
     int k;
@@ -476,13 +483,18 @@ static void or_ct_face_pencil(const or_problem *P, double *const *q, int d, int 
         bp[e] = bf[e] - dt / (2.0 * hd) * (f1[e] - f1[e - 1]);
         wp[e] = vh[e] * bp[e];
     }
-    /* corrector: piecewise-linear TVD flux about the upwind cell */
-    for (e = OR_NG - 1; e < OR_NG + n; ++e) {
-        double vbar = 0.5 * (vh[e] + vh[e + 1]);
-        if (vbar > 0.0)
-            f2[e] = wp[e] + 0.5 * or_limit(P->limiter, wp[e] - wp[e - 1], wp[e + 1] - wp[e]);
-        else
-            f2[e] = wp[e + 1] - 0.5 * or_limit(P->limiter, wp[e + 1] - wp[e], wp[e + 2] - wp[e + 1]);
+    /* corrector: piecewise-linear TVD flux about the upwind cell; the hybrid
+     * limiter takes its subsonic (Van Leer) branch here: the magnetic operator
+     * has no sound speed (reading C-21) */
+    {
+        const int lim = P->limiter == OR_LIM_HYBRID ? OR_LIM_VANLEER : P->limiter;
+        for (e = OR_NG - 1; e < OR_NG + n; ++e) {
+            double vbar = 0.5 * (vh[e] + vh[e + 1]);
+            if (vbar > 0.0)
+                f2[e] = wp[e] + 0.5 * or_limit(lim, wp[e] - wp[e - 1], wp[e + 1] - wp[e]);
+            else
+                f2[e] = wp[e + 1] - 0.5 * or_limit(lim, wp[e + 1] - wp[e], wp[e + 2] - wp[e + 1]);
+        }
     }
     for (e = -1; e < n; ++e) f[e + 1] = f2[e + OR_NG];
 }
@@ -574,14 +586,47 @@ static void or_fields(const or_problem *P, double *state, double *q[8])
     for (f = 0; f < 8; ++f) q[f] = state + (long)f * N;
 }
 
-/* L_d(dt) on every pencil along d.  Returns the OR_FLAG_* bits seen. */
+/* Gravity operator G_d(tau) of the operator-split form (eq02512 with the
+ * centred difference eq02513): the momentum along d takes the impulse of the
+ * potential, rho and the internal energy stay; the total energy changes by
+ * the kinetic energy the impulse adds (the paper's code keeps internal
+ * energy as its variable, Sec. 2.3; reading C-22). */
+static void or_gravity(const or_problem *P, double *const *q, int d, double tau)
+{
+    const long N = (long)P->n[0] * P->n[1] * P->n[2];
+    long idx;
+#pragma omp parallel for schedule(static)
+    for (idx = 0; idx < N; ++idx) {
+        long c[3], cp[3], cm[3];
+        double dphi, mo, mn, rho;
+        int a;
+        c[0] = idx % P->n[0];
+        c[1] = (idx / P->n[0]) % P->n[1];
+        c[2] = idx / ((long)P->n[0] * P->n[1]);
+        for (a = 0; a < 3; ++a) cp[a] = cm[a] = c[a];
+        cp[d] += 1;
+        cm[d] -= 1;
+        dphi = (P->phi[or_index(P, cp[0], cp[1], cp[2])] - P->phi[or_index(P, cm[0], cm[1], cm[2])]) /
+               (2.0 * P->h[d]);
+        rho = q[0][idx];
+        mo = q[1 + d][idx];
+        mn = mo - tau * rho * dphi;
+        q[1 + d][idx] = mn;
+        q[4][idx] = q[4][idx] + 0.5 * (mn * mn - mo * mo) / rho;
+    }
+}
+
+/* L_d(dt) on every pencil along d -- with operator-split gravity the sweep
+ * G_d(dt/2) L_d(dt) G_d(dt/2) (eq025111).  Returns the OR_FLAG_* bits seen. */
 int oracle_fluid(const or_problem *P, double *state, int d, double dt)
 {
     double *q[8];
     const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
     const long n1 = P->n[t1], n2 = P->n[t2];
     int flags = 0, err = 0;
+    const int split = P->phi != NULL && P->gravity_split;
     or_fields(P, state, q);
+    if (split) or_gravity(P, q, d, 0.5 * dt);
 #pragma omp parallel
     {
         or_scratch S;
@@ -598,6 +643,7 @@ int oracle_fluid(const or_problem *P, double *state, int d, double dt)
         }
         or_scratch_free(&S);
     }
+    if (split && !err) or_gravity(P, q, d, 0.5 * dt);
     return err ? -1 : flags;
 }
 

@@ -22,8 +22,11 @@ MUTANTS = {
     "ct_bz_sign_as_printed": ("nb[t2][idx] = q[5 + t2][idx] - dt", "nb[t2][idx] = q[5 + t2][idx] + dt"),
     "ct_constraint_index": ("(fa[s + 1] - fam[s + 1])", "(fa[s + 1] - fam[s])"),
     "ct_face_neighbour": ("cB[d] = s; cB[c] = fc + 1; cB[o] = fo;", "cB[d] = s; cB[c] = fc - 1; cB[o] = fo;"),
-    "minus_slope_sign": ("double slm = or_limit(P->limiter, fm2 - fm1, fm3 - fm2);",
-                         "double slm = or_limit(P->limiter, fm1 - fm2, fm3 - fm2);"),
+    "minus_slope_sign": ("double slm = or_limit(lim, fm2 - fm1, fm3 - fm2);   /* eq0220 */",
+                         "double slm = or_limit(lim, fm1 - fm2, fm3 - fm2);   /* eq0220 */"),
+    "hybrid_criterion_inverted": ("? OR_LIM_MINMOD : OR_LIM_VANLEER;", "? OR_LIM_VANLEER : OR_LIM_MINMOD;"),
+    "split_gravity_sign": ("mn = mo - tau * rho * dphi;", "mn = mo + tau * rho * dphi;"),
+    "split_gravity_energy_dropped": ("q[4][idx] = q[4][idx] + 0.5 * (mn * mn - mo * mo) / rho;", "(void)mo;"),
     "slopes_added": ("F[k] = fp1 + fm2 + 0.5 * (slp - slm);", "F[k] = fp1 + fm2 + 0.5 * (slp + slm);"),
     "freezing_speed_wrong_interface": ("double D = fmax(c1->d, c2->d);", "double D = fmax(c0->d, c1->d);"),
     "predictor_full_step": ("up[k] = u[k * m + e] - dt / (2.0 * hd) *", "up[k] = u[k * m + e] - dt / hd *"),
@@ -179,10 +182,37 @@ def battery(oracle_mod, lib):
         ob.step(0.01, 2)
         return np.array_equal(ob.state, st)
 
+    def hybrid():
+        ok = True
+        for vel, lim in ((0.5, 0), (3.0, 1)):
+            w = W.entropy_wave(24, axis=0, ntrans=4, vel=vel)
+            a = _box(oracle_mod, lib, w, limiter=3)
+            b = _box(oracle_mod, lib, w, limiter=lim)
+            dt = a.cfl(0.5)
+            a.step(dt)
+            b.step(dt)
+            ok = ok and np.array_equal(a.state, b.state)
+        return ok
+
+    def splitfall():
+        n, g, rho, p = 16, 0.7, 1.3, 2.0
+        shape = (1, 1, n)
+        x = (np.arange(n) + 0.5) / n
+        st = W.assemble(np.full(shape, rho), (0.0, 0.0, 0.0), p, (0.0, 0.0, 0.0), 5 / 3, W.BC_OUTFLOW)
+        w = W.Workload("sf", st, 5 / 3, (1.0 / n, 1, 1), bc=W.BC_OUTFLOW, phi=np.broadcast_to(g * x, shape).copy())
+        ob = _box(oracle_mod, lib, w, gravity_split=True)
+        dt = 0.01
+        ob.fluid(0, dt)
+        s = slice(4, n - 4)
+        return (np.allclose(ob.state[1, 0, 0, s], -rho * g * dt, rtol=1e-13, atol=0)
+                and np.allclose(ob.state[4, 0, 0, s], p / (2 / 3) + 0.5 * (rho * g * dt) ** 2 / rho,
+                                rtol=1e-13, atol=0))
+
     for name, fn in [("alfven", alfven), ("oblique", oblique), ("fastwave", fastwave),
                      ("entropy", entropy), ("sod", sod),
                      ("invariants", invariants), ("freefall", freefall), ("cfl", cfl),
-                     ("atmosphere", atmosphere), ("rusanov", rusanov), ("uniform", uniform)]:
+                     ("atmosphere", atmosphere), ("rusanov", rusanov), ("uniform", uniform),
+                     ("hybrid", hybrid), ("splitfall", splitfall)]:
         try:
             with np.errstate(all="ignore"):
                 ok = bool(fn())
