@@ -57,15 +57,23 @@ enum { FISH_BC_PERIODIC = 0, FISH_BC_OUTFLOW = 1 };
 enum {
     FISH_OPT_PRECISION = 0,  /* FISH_PREC_FP64 (default) or FISH_PREC_FP32 */
     FISH_OPT_LIMITER = 1,    /* FISH_LIM_VANLEER (default, eq0200), FISH_LIM_MINMOD (eq0190),
-                                FISH_LIM_NONE (first order, eq0140) */
+                                FISH_LIM_NONE (first order, eq0140), FISH_LIM_HYBRID (Sec. 2.2:
+                                minmod at interfaces where either cell has |v_d| > c_S, Van
+                                Leer elsewhere; the constrained transport keeps Van Leer) */
     FISH_OPT_HSE = 2,        /* 1: hydrostatic-gradient correction, eq0321-eq03261 */
     FISH_OPT_PRED_DISS = 3,  /* predictor freezing-speed factor in [0,1] (Sec. 2.2); default 1 */
     FISH_OPT_DX = 4,         /* cell widths; default 1/nx, 1/ny, 1/nz */
     FISH_OPT_DY = 5,
-    FISH_OPT_DZ = 6
+    FISH_OPT_DZ = 6,
+    FISH_OPT_GRAVITY = 7     /* FISH_GRAV_UNSPLIT (default): potential source terms inside L_d
+                                (eq0253-eq0255); FISH_GRAV_SPLIT: L_d becomes G_d(dt/2) L_d G_d(dt/2)
+                                with G_d: m_d -= (dt/2) rho dphi/dx_d (centred difference) and E
+                                changed by the kinetic energy change (eq025111-eq02513).  Split
+                                gravity and FISH_OPT_HSE = 1 exclude each other (FISH_ERR_ARG). */
 };
+enum { FISH_GRAV_UNSPLIT = 0, FISH_GRAV_SPLIT = 1 };
 enum { FISH_PREC_FP64 = 0, FISH_PREC_FP32 = 1 };
-enum { FISH_LIM_VANLEER = 0, FISH_LIM_MINMOD = 1, FISH_LIM_NONE = 2 };
+enum { FISH_LIM_VANLEER = 0, FISH_LIM_MINMOD = 1, FISH_LIM_NONE = 2, FISH_LIM_HYBRID = 3 };
 
 /* dtype codes of device buffers */
 enum { FISH_F64 = 0, FISH_F32 = 1 };

@@ -21,9 +21,11 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfish.so")
 
 FISH_OK, FISH_ERR_ARG, FISH_ERR_CUDA, FISH_ERR_OOM, FISH_ERR_STATE, FISH_ERR_NONPHYSICAL, FISH_ERR_TIMEOUT = range(7)
 FISH_BC_PERIODIC, FISH_BC_OUTFLOW = 0, 1
-FISH_OPT_PRECISION, FISH_OPT_LIMITER, FISH_OPT_HSE, FISH_OPT_PRED_DISS, FISH_OPT_DX, FISH_OPT_DY, FISH_OPT_DZ = range(7)
+(FISH_OPT_PRECISION, FISH_OPT_LIMITER, FISH_OPT_HSE, FISH_OPT_PRED_DISS, FISH_OPT_DX, FISH_OPT_DY, FISH_OPT_DZ,
+ FISH_OPT_GRAVITY) = range(8)
 FISH_PREC_FP64, FISH_PREC_FP32 = 0, 1
-FISH_LIM_VANLEER, FISH_LIM_MINMOD, FISH_LIM_NONE = 0, 1, 2
+FISH_LIM_VANLEER, FISH_LIM_MINMOD, FISH_LIM_NONE, FISH_LIM_HYBRID = 0, 1, 2, 3
+FISH_GRAV_UNSPLIT, FISH_GRAV_SPLIT = 0, 1
 FISH_F64, FISH_F32 = 0, 1
 FISH_OP_FLUID, FISH_OP_CT = 0, 1
 FISH_BATCH_OPT_LIMITER, FISH_BATCH_OPT_ORDER, FISH_BATCH_OPT_GROUPS, FISH_BATCH_OPT_GRID = range(4)
@@ -120,7 +122,7 @@ class Box:
     (faces i+1/2), b_y (faces j+1/2), b_z (faces k+1/2)."""
 
     def __init__(self, nx, ny, nz, gamma, bc=FISH_BC_PERIODIC, precision="fp64", limiter=FISH_LIM_VANLEER,
-                 hse=False, pred_diss=1.0, h=None, use_torch_allocator=True, stream=None):
+                 hse=False, pred_diss=1.0, h=None, use_torch_allocator=True, stream=None, gravity="unsplit"):
         self._lib = load()
         self.n = (int(nx), int(ny), int(nz))
         self.precision = precision
@@ -135,6 +137,9 @@ class Box:
                 raise ValueError("precision must be 'fp64' or 'fp32'")
             self.set_option(FISH_OPT_PRECISION, FISH_PREC_FP64 if precision == "fp64" else FISH_PREC_FP32)
             self.set_option(FISH_OPT_LIMITER, int(limiter))
+            if gravity not in ("unsplit", "split"):
+                raise ValueError("gravity must be 'unsplit' or 'split'")
+            self.set_option(FISH_OPT_GRAVITY, FISH_GRAV_SPLIT if gravity == "split" else FISH_GRAV_UNSPLIT)
             self.set_option(FISH_OPT_HSE, 1 if hse else 0)
             self.set_option(FISH_OPT_PRED_DISS, float(pred_diss))
             if h is not None:

@@ -31,6 +31,7 @@ struct fish_ctx {
     int prec = FISH_PREC_FP64;
     int lim = FISH_LIM_VANLEER;
     int hse = 0;
+    int gsplit = 0;        // FISH_GRAV_SPLIT: gravity as G_d(dt/2) L_d G_d(dt/2)
     double alpha = 1.0;
     double h[3] = {0, 0, 0};
 
@@ -242,8 +243,25 @@ template <class T> const T *sweep_potential(const fish_ctx *c, int d)
     return (const T *)(c->layout ? c->phiT : c->phi);
 }
 
+// G_d(dt/2) in place on the current fluid buffer (operator-split gravity)
+template <class T> int op_gravity(fish_ctx *c, int d)
+{
+    T *u[5];
+    for (int f = 0; f < 5; ++f) u[f] = (T *)c->fl[c->cu][f];
+    FISH_CK(c, Launch<T>::gravity(u, sweep_potential<T>(c, d), c->dt_dev, 0.5, geom(c), d, c->h[d], c->stream),
+            "gravity launch");
+    c->launches += 1;
+    return FISH_OK;
+}
+
+bool split_gravity(const fish_ctx *c) { return c->gsplit && c->has_phi; }
+
+// L_d, or G_d(dt/2) L_d G_d(dt/2) with operator-split gravity (eq025111)
 template <class T> int op_fluid(fish_ctx *c, int d, bool fuse_cfl)
 {
+    const bool split = split_gravity(c);
+    int r;
+    if (split && (r = op_gravity<T>(c, d))) return r;
     const T *in[8];
     T *out[5];
     for (int f = 0; f < 5; ++f) {
@@ -252,12 +270,13 @@ template <class T> int op_fluid(fish_ctx *c, int d, bool fuse_cfl)
     }
     for (int f = 0; f < 3; ++f) in[5 + f] = (const T *)c->bf[c->cb][f];
     FISH_CK(c,
-            Launch<T>::fluid(in, out, sweep_potential<T>(c, d), c->dt_dev,
+            Launch<T>::fluid(in, out, split ? nullptr : sweep_potential<T>(c, d), c->dt_dev,
                              geom(c), d, c->lim, c->hse != 0, c->gamma, c->alpha, c->h, c->flags,
                              fuse_cfl ? c->minbits : nullptr, c->stream),
             "fluid sweep launch");
     c->cu = 1 - c->cu;
     c->launches += 1;
+    if (split && (r = op_gravity<T>(c, d))) return r;
     return FISH_OK;
 }
 
@@ -291,7 +310,7 @@ int apply_op(fish_ctx *c, int op, int d, bool fuse_cfl = false)
 // minimum of the new state (FP32 two-column kernels only).
 bool last_sweep_fuses_cfl(const fish_ctx *c)
 {
-    if (c->prec != FISH_PREC_FP32) return false;
+    if (c->prec != FISH_PREC_FP32 || split_gravity(c)) return false;
     return Launch<float>::fluid_fuses_cfl(geom_of(c, layout_for(0)), 0, c->lim, c->hse != 0);
 }
 
@@ -390,12 +409,19 @@ int fish_set_option(fish_ctx *c, int key, double v)
         c->prec = (int)v;
         break;
     case FISH_OPT_LIMITER:
-        if (v != 0 && v != 1 && v != 2) return fail(c, FISH_ERR_ARG, "bad limiter");
+        if (v != FISH_LIM_VANLEER && v != FISH_LIM_MINMOD && v != FISH_LIM_NONE && v != FISH_LIM_HYBRID)
+            return fail(c, FISH_ERR_ARG, "bad limiter");
         c->lim = (int)v;
         break;
     case FISH_OPT_HSE:
         if (v != 0 && v != 1) return fail(c, FISH_ERR_ARG, "bad HSE switch");
+        if (v == 1 && c->gsplit) return fail(c, FISH_ERR_ARG, "HSE correction needs unsplit gravity");
         c->hse = (int)v;
+        break;
+    case FISH_OPT_GRAVITY:
+        if (v != FISH_GRAV_UNSPLIT && v != FISH_GRAV_SPLIT) return fail(c, FISH_ERR_ARG, "bad gravity mode");
+        if (v == FISH_GRAV_SPLIT && c->hse) return fail(c, FISH_ERR_ARG, "HSE correction needs unsplit gravity");
+        c->gsplit = (int)v;
         break;
     case FISH_OPT_PRED_DISS:
         if (!(v >= 0.0 && v <= 1.0)) return fail(c, FISH_ERR_ARG, "predictor factor outside [0,1]");

@@ -254,11 +254,18 @@ __device__ __forceinline__ void cflux1(const CCell<V> &a, const CCell<V> &b, V p
 
 // second-order TVD flux at the interface c1|c2 from predicted cells c0..c3
 // (eq0160-eq0230; one freezing speed per interface, reading C-2; HSE form of
-// the slope differences, reading C-19)
+// the slope differences, reading C-19).  The hybrid limiter is taken only by
+// the one-column kernels with the limiter read at run time.
 template <class V, bool HSE, int LIM>
 __device__ __forceinline__ void cflux2(const CCell<V> &c0, const CCell<V> &c1, const CCell<V> &c2, const CCell<V> &c3,
                                        V ph0, V ph1, V ph2, V ph3, V F[5], int lim)
 {
+    if constexpr (LIM < 0 && VT<V>::W == 1) {
+        // hybrid limiter (Sec. 2.2): minmod where either cell of the
+        // interface moves faster than its sound speed, else Van Leer (reading C-21)
+        if (lim == LIM_HYBRID)
+            lim = (vabs(c1.vn) > c1.cs || vabs(c2.vn) > c2.cs) ? LIM_MINMOD : LIM_VANLEER;
+    }
     if constexpr (!HSE && !VT<V>::F64) {
         // FP32: F = (F_e + F_{e+1})/2 - D du_e/2 + [phi(+) - phi(-)]/4 with the
         // split-flux slopes written as dF +- D du (each one multiply-add)

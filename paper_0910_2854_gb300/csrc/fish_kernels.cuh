@@ -629,6 +629,55 @@ __global__ void __launch_bounds__(256) transpose_kernel(TransArgs<T> A)
 }
 
 // ---------------------------------------------------------------------------
+// operator-split gravity G_d(tau) (eq025111-eq02513): in place on the current
+// state, m_d -= tau rho dphi/dx_d with the centred potential difference, and
+// E changes by the kinetic energy change (reading C-22), tau = frac * dt.
+// FP64 reads the cell potential in the current layout; FP32 the differences
+// to the next cell along d (formed in FP64), phi_{i+1} - phi_{i-1} = D_i +
+// D_{i-1} with D_{-1} = 0 at an outflow boundary.
+// ---------------------------------------------------------------------------
+template <class T> struct GravArgs {
+    const T *rho;
+    T *md, *E;
+    const T *phi;
+    const double *dt;
+    double frac;
+    long long N, sd;
+    int n, bc;
+    double h;
+};
+
+template <class T>
+__global__ void __launch_bounds__(256) gravity_kernel(GravArgs<T> A)
+{
+    const double tau = A.frac * *A.dt;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)((i / A.sd) % A.n);
+        if constexpr (sizeof(T) == 8) {
+            const long long ip = i + (long long)(gmap(s + 1, A.n, A.bc) - s) * A.sd;
+            const long long im = i + (long long)(gmap(s - 1, A.n, A.bc) - s) * A.sd;
+            const double dphi = (A.phi[ip] - A.phi[im]) / (2.0 * A.h);
+            const double rho = A.rho[i];
+            const double mo = A.md[i];
+            const double mn = mo - tau * rho * dphi;
+            A.md[i] = mn;
+            A.E[i] = A.E[i] + 0.5 * (mn * mn - mo * mo) / rho;
+        } else {
+            float dm1;
+            if (s > 0) dm1 = A.phi[i - A.sd];
+            else dm1 = A.bc == BC_PERIODIC ? A.phi[i + (long long)(A.n - 1) * A.sd] : 0.0f;
+            const float dphi = (A.phi[i] + dm1) * (float)(0.5 / A.h);
+            const float rho = A.rho[i];
+            const float mo = A.md[i];
+            const float dm = -((float)tau * rho) * dphi;
+            A.md[i] = mo + dm;
+            A.E[i] = A.E[i] + dm * (mo + 0.5f * dm) / rho;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // precision conversion of one field
 // ---------------------------------------------------------------------------
 template <class S, class D>

@@ -42,13 +42,13 @@ static inline bool frame_of(const Geom &g, int d, Frame &F)
 }
 
 // The two-column FP32 kernels are used for even fast extents without the
-// hydrostatic correction and with a limiter.
+// hydrostatic correction and with the Van Leer or minmod limiter.
 template <class T> static bool uses_pairs(const Frame &F, int lim, bool hse)
 {
 #ifdef FISH_FLUID_SCALAR
     return false;
 #else
-    return sizeof(T) == 4 && F.nf % 2 == 0 && !hse && lim != LIM_NONE;
+    return sizeof(T) == 4 && F.nf % 2 == 0 && !hse && (lim == LIM_VANLEER || lim == LIM_MINMOD);
 #endif
 }
 
@@ -134,6 +134,9 @@ cudaError_t Launch<T>::ct(const T *rho, const T *md, const T *const b[3], T *con
     A.nf = F.nf;
     A.no = F.no;
     A.bc = g.bc;
+    // the hybrid limiter steers the fluid fluxes only; the face fluxes of
+    // the constrained transport keep Van Leer (reading C-21)
+    if (lim == LIM_HYBRID) lim = LIM_VANLEER;
     A.lim = lim;
     A.h = h[d];
     A.hf = h[F.fast];
@@ -195,6 +198,29 @@ cudaError_t Launch<T>::transpose(const T *const src[8], T *const dst[8], int nf,
     A.plane = (long long)nr * nc;
     dim3 grid((nr + 31) / 32, (nc + 31) / 32, nz);
     transpose_kernel<T><<<grid, dim3(32, 8), 0, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t Launch<T>::gravity(T *const u[5], const T *phi, const double *dt, double frac, const Geom &g, int d,
+                               double h, cudaStream_t s)
+{
+    if (!phi || d < 0 || d > 2) return cudaErrorInvalidValue;
+    GravArgs<T> A;
+    A.rho = u[0];
+    A.md = u[1 + d];
+    A.E = u[4];
+    A.phi = phi;
+    A.dt = dt;
+    A.frac = frac;
+    A.N = (long long)g.n[0] * g.n[1] * g.n[2];
+    A.sd = g.st[d];
+    A.n = g.n[d];
+    A.bc = g.bc;
+    A.h = h;
+    unsigned gr = grid_for(A.N, 256);
+    if (gr > 152u * 16u) gr = 152u * 16u;
+    gravity_kernel<T><<<gr, 256, 0, s>>>(A);
     return cudaGetLastError();
 }
 

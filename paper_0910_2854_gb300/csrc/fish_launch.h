@@ -31,6 +31,10 @@ template <class T> struct Launch {
     // per z-plane transpose of the 8 fields: nc rows of nr -> nr rows of nc
     static cudaError_t transpose(const T *const src[8], T *const dst[8], int nf, int nr, int nc, int nz,
                                  cudaStream_t s);
+    // G_d(frac * dt) in place on u[5] (operator-split gravity); phi as the
+    // fluid sweep of d reads it (FP64 potential, FP32 differences along d)
+    static cudaError_t gravity(T *const u[5], const T *phi, const double *dt, double frac, const Geom &g, int d,
+                               double h, cudaStream_t s);
     static cudaError_t from_f64(const double *src, T *dst, long long n, cudaStream_t s);
     static cudaError_t from_f32(const float *src, T *dst, long long n, cudaStream_t s);
     static cudaError_t to_f64(const T *src, double *dst, long long n, cudaStream_t s);

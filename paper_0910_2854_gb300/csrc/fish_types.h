@@ -5,7 +5,7 @@ namespace fish {
 
 // sticky device status bits (reading C-16: no floor, report instead)
 enum : unsigned { FLAG_RHO = 1u, FLAG_P = 2u, FLAG_NAN = 4u, FLAG_TIMEOUT = 8u };
-enum : int { LIM_VANLEER = 0, LIM_MINMOD = 1, LIM_NONE = 2 };
+enum : int { LIM_VANLEER = 0, LIM_MINMOD = 1, LIM_NONE = 2, LIM_HYBRID = 3 };
 enum : int { BC_PERIODIC = 0, BC_OUTFLOW = 1 };
 
 // Box geometry: cell counts n[axis], element strides st[axis] of the

@@ -304,3 +304,131 @@ def test_bad_arguments_rejected(F):
     with pytest.raises(F.FishError):
         box.set_option(99, 1.0)
     box.close()
+
+
+# ---------------------------------------------------------------------------
+# hybrid limiter and operator-split gravity
+# ---------------------------------------------------------------------------
+
+def mixed_mach(nx, ny, nz, seed, bc=W.BC_PERIODIC):
+    """Random smooth flow with velocities up to about twice the sound speed:
+    sub- and supersonic interfaces side by side (with Van Leer everywhere
+    this flow reaches p < 0 within three steps; the hybrid limiter keeps it
+    positive)."""
+    return W.random_smooth(nx, ny, nz, seed=seed, vamp=1.0, bc=bc)
+
+
+def test_mixed_mach_workload_has_both_regimes():
+    w = mixed_mach(24, 20, 18, seed=51)
+    st = w.state
+    v = np.abs(st[1:4] / st[0])
+    bc = np.array(W.cell_centred(st[5:8], w.bc))
+    p = (w.gamma - 1) * (st[4] - 0.5 * np.sum(st[1:4] ** 2, axis=0) / st[0] - 0.5 * np.sum(bc ** 2, axis=0))
+    cs = np.sqrt(w.gamma * p / st[0])
+    frac = np.mean(v > cs)
+    assert 0.05 < frac < 0.95, frac
+
+
+@pytest.mark.parametrize("bc", [W.BC_PERIODIC, W.BC_OUTFLOW])
+def test_hybrid_limiter_fp64(F, bc):
+    w = mixed_mach(23, 18, 14, seed=52, bc=bc)
+    ob, gb = pair(F, w, limiter=F.FISH_LIM_HYBRID)
+    for _ in range(3):
+        dt = ob.cfl(0.4)
+        ob.step(dt)
+        gb.step(dt)
+    assert ob.flags == 0
+    assert rel_err(gb.get_state(), ob.state) <= 1e-12
+    gb.close()
+
+
+@pytest.mark.parametrize("box", sorted(FP32_BOXES))
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_hybrid_limiter_fp32_fluid(F, box, d):
+    """FP32 one-column kernels with the limiter chosen per interface, against
+    the oracle after one L_d (the face fluxes of B_d keep Van Leer)."""
+    w = FP32_BOXES[box]()
+    st = w.state.copy()
+    st[1:4] *= 5.0  # |v| ~ c_S: both regimes
+    st[4] += 0.5 * np.sum(st[1:4] ** 2, axis=0) / st[0] * (1 - 1 / 25.0)
+    w = W.Workload(w.name, st, w.gamma, w.h, w.bc)
+    ob, gb = pair(F, w, precision="fp32", limiter=F.FISH_LIM_HYBRID)
+    dt = 0.3 * ob.cfl(1.0)
+    ob.fluid(d, dt)
+    gb.fluid(d, dt)
+    assert rel_err(gb.get_state(), ob.state) <= 1e-5
+    gb.close()
+
+
+def test_hybrid_limiter_ct_keeps_van_leer(F):
+    w = mixed_mach(16, 14, 12, seed=53)
+    out = {}
+    for lim in (F.FISH_LIM_HYBRID, F.FISH_LIM_VANLEER):
+        gb = F.Box(*w.dims, w.gamma, bc=w.bc, h=w.h, limiter=lim)
+        gb.set_state(w.state)
+        gb.ct(1, 1e-3)
+        out[lim] = gb.get_state()
+        gb.close()
+    assert np.array_equal(out[F.FISH_LIM_HYBRID], out[F.FISH_LIM_VANLEER])
+
+
+def split_pair(F, w, precision):
+    ob = oracle.OracleBox(*w.dims, w.gamma, bc=w.bc, h=w.h, phi=w.phi, gravity_split=True)
+    ob.set_state(w.state)
+    gb = F.Box(*w.dims, w.gamma, bc=w.bc, precision=precision, h=w.h, gravity="split")
+    gb.set_state(w.state)
+    gb.set_potential(w.phi)
+    return ob, gb
+
+
+def periodic_well(nx, ny, nz, seed):
+    """Random smooth periodic state in a smooth periodic potential well."""
+    w = W.random_smooth(nx, ny, nz, seed=seed)
+    z, y, x = np.meshgrid((np.arange(nz) + 0.5) / nz, (np.arange(ny) + 0.5) / ny, (np.arange(nx) + 0.5) / nx,
+                          indexing="ij")
+    phi = -0.8 * np.cos(2 * np.pi * x) * np.cos(2 * np.pi * y) + 0.3 * np.sin(2 * np.pi * z)
+    return W.Workload("well", w.state, w.gamma, w.h, w.bc, phi=phi)
+
+
+SPLIT_BOXES = {"polytrope": lambda: W.polytrope(24), "periodic_well": lambda: periodic_well(22, 17, 13, seed=54)}
+
+
+@pytest.mark.parametrize("box", sorted(SPLIT_BOXES))
+def test_split_gravity_fp64(F, box):
+    w = SPLIT_BOXES[box]()
+    ob, gb = split_pair(F, w, "fp64")
+    for _ in range(4):
+        dt = ob.cfl(0.5)
+        ob.step(dt)
+        gb.step(dt)
+    assert ob.flags == 0
+    assert rel_err(gb.get_state(), ob.state) <= 1e-12
+    gb.close()
+
+
+@pytest.mark.parametrize("box", sorted(SPLIT_BOXES))
+def test_split_gravity_fp32(F, box):
+    """FP32: the fluid sweeps run without source terms (two-column kernels
+    where the extent is even) between two in-place G_d(dt/2); the graph step
+    with its own CFL must follow the host loop."""
+    w = SPLIT_BOXES[box]()
+    ob, gb = split_pair(F, w, "fp32")
+    for _ in range(2):
+        dt = ob.cfl(0.5)
+        ob.step(dt)
+        gb.step(dt)
+    assert rel_err(gb.get_state(), ob.state) <= 1e-5
+    gb.close()
+    ob, gb = split_pair(F, w, "fp32")
+    gb.step_cfl(0.5, 2)
+    for _ in range(2):
+        ob.step(ob.cfl(0.5))
+    assert rel_err(gb.get_state(), ob.state) <= 1e-5
+    gb.close()
+
+
+def test_split_gravity_excludes_hse(F):
+    w = W.polytrope(8)
+    with pytest.raises(F.FishError) as ei:
+        F.Box(*w.dims, w.gamma, bc=w.bc, gravity="split", hse=True)
+    assert ei.value.code == F.FISH_ERR_ARG
