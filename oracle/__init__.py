@@ -89,7 +89,8 @@ class _Problem(ctypes.Structure):
                 ("limiter", ctypes.c_int), ("hse", ctypes.c_int),
                 ("pred_diss", ctypes.c_double),
                 ("phi", ctypes.POINTER(ctypes.c_double)),
-                ("gravity_split", ctypes.c_int)]
+                ("gravity_split", ctypes.c_int),
+                ("w", ctypes.POINTER(ctypes.c_double) * 3)]
 
 
 def _bind(lib):
@@ -133,7 +134,8 @@ class OracleBox:
     """
 
     def __init__(self, nx, ny, nz, gamma, bc=BC_PERIODIC, h=None,
-                 limiter=LIM_VANLEER, hse=False, pred_diss=1.0, phi=None, gravity_split=False, lib=None):
+                 limiter=LIM_VANLEER, hse=False, pred_diss=1.0, phi=None, gravity_split=False, widths=None,
+                 lib=None):
         self._lib = lib
         self.n = (int(nx), int(ny), int(nz))
         if h is None:
@@ -147,6 +149,15 @@ class OracleBox:
         self.gravity_split = bool(gravity_split)
         self.state = np.zeros((8, nz, ny, nx), dtype=np.float64)
         self.phi = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64).reshape(nz, ny, nx)
+        # irregular Cartesian mesh (eq037): per axis None (uniform h) or the cell widths
+        self.widths = [None, None, None]
+        if widths is not None:
+            for d, wd in enumerate(widths):
+                if wd is not None:
+                    wd = np.ascontiguousarray(wd, dtype=np.float64).reshape(-1)
+                    if wd.size != self.n[d] or not np.all(wd > 0):
+                        raise ValueError("widths[%d] needs %d positive entries" % (d, self.n[d]))
+                    self.widths[d] = wd
         self.flags = 0
 
     # -- marshalling -------------------------------------------------------
@@ -167,6 +178,10 @@ class OracleBox:
             p.phi = self.phi.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         else:
             p.phi = ctypes.POINTER(ctypes.c_double)()
+        for d in range(3):
+            wd = self.widths[d]
+            p.w[d] = (wd.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if wd is not None
+                      else ctypes.POINTER(ctypes.c_double)())
         return p
 
     def _ptr(self):

@@ -18,7 +18,9 @@
  *     (eq0253-eq0255) and the hydrostatic-gradient correction
  *     (eq0321-eq03261);
  *   - B_d: constrained transport (eq0330-eq0364);
- *   - CFL time step (eq0083-eq0084).
+ *   - CFL time step (eq0083-eq0084);
+ *   - irregular Cartesian meshes (Sec. 2.5, eq037, eq0420): cell widths per
+ *     axis, readings C-23 .. C-27.
  * Equations are cited by the paper's LaTeX labels.
  * Where the paper is silent, garbled or inconsistent, the reading used is
  * named C-n in the comments; each is listed with its justification in the
@@ -53,6 +55,7 @@ typedef struct {
     double pred_diss;    /* predictor freezing-speed factor in [0,1] (Sec. 2.2, predictor step) */
     const double *phi;   /* NULL or cell-centred potential, nx*ny*nz */
     int gravity_split;   /* 1: operator-split gravity G(dt/2) L G(dt/2) (eq025111-eq02513) */
+    const double *w[3];  /* NULL (uniform h[d]) or the n[d] cell widths along axis d (eq037) */
 } or_problem;
 
 /* ------------------------------------------------------------------------ */
@@ -72,6 +75,21 @@ static long or_map(long s, long n, int bc)
     if (s < 0) return 0;
     if (s >= n) return n - 1;
     return s;
+}
+
+/* Width of cell s along axis d: a ghost has the width of the cell it copies
+ * (the periodic image, or the boundary cell for outflow; reading C-23). */
+static double or_width(const or_problem *P, int d, long s)
+{
+    return P->w[d] ? P->w[d][or_map(s, P->n[d], P->bc)] : P->h[d];
+}
+
+/* Distance between the centres of cells s-1 and s+1 along d (the centred
+ * potential difference, eq02513, on an irregular mesh; reading C-26). */
+static double or_centre_span(const or_problem *P, int d, long s)
+{
+    if (!P->w[d]) return 2.0 * P->h[d];
+    return 0.5 * or_width(P, d, s - 1) + or_width(P, d, s) + 0.5 * or_width(P, d, s + 1);
 }
 
 static long or_index(const or_problem *P, long c0, long c1, long c2)
@@ -240,9 +258,22 @@ static void or_flux1(const or_problem *P, const or_cell *a, const or_cell *b,
  * order fluxes are constructed in the same way ... but with the HSE
  * corrected first order fluxes"). */
 static void or_flux2(const or_problem *P, const or_cell *c0, const or_cell *c1,
-                     const or_cell *c2, const or_cell *c3, const double ph[4], double F[5])
+                     const or_cell *c2, const or_cell *c3, const double ph[4], const double *dw,
+                     double F[5])
 {
     int k;
+    /* irregular mesh (reading C-25): each one-sided difference is divided by
+     * the distance between the centres it joins and the limited slope is
+     * carried over half the width of its own cell (c1 for F+, c2 for F-);
+     * uniform widths reduce this to eq0230 */
+    double sp = 1.0, sm = 1.0, gl = 1.0, gc = 1.0, gr = 1.0;
+    if (dw) {
+        sp = dw[1];
+        sm = dw[2];
+        gl = 0.5 * (dw[0] + dw[1]);
+        gc = 0.5 * (dw[1] + dw[2]);
+        gr = 0.5 * (dw[2] + dw[3]);
+    }
     /* hybrid limiter (Sec. 2.2, after eq0200): Van Leer where the flow is
      * subsonic, minmod where it is supersonic; decided per interface from the
      * two cells that share it (reading C-21) */
@@ -258,8 +289,14 @@ static void or_flux2(const or_problem *P, const or_cell *c0, const or_cell *c1,
             double fm1 = 0.5 * (c1->F[k] - D * c1->u[k]);
             double fm2 = 0.5 * (c2->F[k] - D * c2->u[k]);
             double fm3 = 0.5 * (c3->F[k] - D * c3->u[k]);
-            double slp = or_limit(lim, fp1 - fp0, fp2 - fp1);   /* eq0180 */
-            double slm = or_limit(lim, fm2 - fm1, fm3 - fm2);   /* eq0220 */
+            double slp, slm;
+            if (!dw) {
+                slp = or_limit(lim, fp1 - fp0, fp2 - fp1);   /* eq0180 */
+                slm = or_limit(lim, fm2 - fm1, fm3 - fm2);   /* eq0220 */
+            } else {
+                slp = sp * or_limit(lim, (fp1 - fp0) / gl, (fp2 - fp1) / gc);
+                slm = sm * or_limit(lim, (fm2 - fm1) / gc, (fm3 - fm2) / gr);
+            }
             F[k] = fp1 + fm2 + 0.5 * (slp - slm);                      /* eq0230 */
         }
     } else {
@@ -277,8 +314,14 @@ static void or_flux2(const or_problem *P, const or_cell *c0, const or_cell *c1,
             double fp_r = 0.5 * ((c2->F[k] - c1->F[k]) + q1);  /* F+_{e+1} - F+_e    */
             double fm_l = 0.5 * ((c2->F[k] - c1->F[k]) - q1);  /* F-_{e+1} - F-_e    */
             double fm_r = 0.5 * ((c3->F[k] - c2->F[k]) - q2);  /* F-_{e+2} - F-_{e+1} */
-            double slp = or_limit(lim, fp_l, fp_r);
-            double slm = or_limit(lim, fm_l, fm_r);
+            double slp, slm;
+            if (!dw) {
+                slp = or_limit(lim, fp_l, fp_r);
+                slm = or_limit(lim, fm_l, fm_r);
+            } else {
+                slp = sp * or_limit(lim, fp_l / gl, fp_r / gc);
+                slm = sm * or_limit(lim, fm_l / gc, fm_r / gr);
+            }
             F[k] = 0.5 * (c1->F[k] + c2->F[k]) - 0.5 * q1 + 0.5 * (slp - slm);
         }
     }
@@ -297,6 +340,7 @@ typedef struct {
     double *up;                  /* predicted states, [5][m] */
     double *F2;                  /* corrector fluxes, [5][m] */
     double *vt, *bf, *w, *f1, *bp, *wp, *f2, *vh; /* constrained transport, [m] each */
+    double *dw;                  /* cell widths along the pencil, [m] */
 } or_scratch;
 
 static int or_scratch_init(or_scratch *s, long n)
@@ -320,15 +364,16 @@ static int or_scratch_init(or_scratch *s, long n)
     s->wp = (double *)calloc(m, sizeof(double));
     s->f2 = (double *)calloc(m, sizeof(double));
     s->vh = (double *)calloc(m, sizeof(double));
+    s->dw = (double *)calloc(m, sizeof(double));
     return (s->u && s->bb && s->ph && s->c0 && s->c1 && s->F1 && s->up && s->F2 && s->vt &&
-            s->bf && s->w && s->f1 && s->bp && s->wp && s->f2 && s->vh) ? 0 : -1;
+            s->bf && s->w && s->f1 && s->bp && s->wp && s->f2 && s->vh && s->dw) ? 0 : -1;
 }
 
 static void or_scratch_free(or_scratch *s)
 {
     free(s->u); free(s->bb); free(s->ph); free(s->c0); free(s->c1); free(s->F1);
     free(s->up); free(s->F2); free(s->vt); free(s->bf); free(s->w); free(s->f1);
-    free(s->bp); free(s->wp); free(s->f2); free(s->vh);
+    free(s->bp); free(s->wp); free(s->f2); free(s->vh); free(s->dw);
 }
 
 /* Fluid operator L_d(dt) for the pencil along axis d at transverse position
@@ -343,10 +388,13 @@ static int or_fluid_pencil(const or_problem *P, double *const *q, int d, long a,
     const double hd = P->h[d];
     const double alpha = P->pred_diss;
     const int grav = P->phi != NULL && !P->gravity_split;  /* unsplit source terms */
+    const int nu = P->w[d] != NULL;                          /* irregular mesh along d */
     int flags = 0;
     long e;
     int k;
-    double *u = S->u, *bb = S->bb, *ph = S->ph;
+    double *u = S->u, *bb = S->bb, *ph = S->ph, *dw = S->dw;
+
+    for (e = 0; e < m; ++e) dw[e] = or_width(P, d, e - OR_NG);
 
     /* gather: conserved state in the sweep frame and the cell-centred field
      * b_bar_c = (b_c at face c-1/2 + b_c at face c+1/2)/2 along each axis c */
@@ -398,10 +446,11 @@ static int or_fluid_pencil(const or_problem *P, double *const *q, int d, long a,
      * source of eq0254, sign as reading C-6) */
     for (e = 1; e + 1 < m; ++e) {
         double up[5], be[3];
+        const double he = nu ? dw[e] : hd;                   /* eq037: the cell's own width */
         for (k = 0; k < 5; ++k)
-            up[k] = u[k * m + e] - dt / (2.0 * hd) * (S->F1[k * m + e] - S->F1[k * m + e - 1]);
+            up[k] = u[k * m + e] - dt / (2.0 * he) * (S->F1[k * m + e] - S->F1[k * m + e - 1]);
         if (grav) {
-            double dphi = (ph[e + 1] - ph[e - 1]) / (2.0 * hd);
+            double dphi = (ph[e + 1] - ph[e - 1]) / or_centre_span(P, d, e - OR_NG);
             up[1] = up[1] - 0.5 * dt * u[0 * m + e] * dphi;
             up[4] = up[4] - 0.5 * dt * u[1 * m + e] * dphi;
         }
@@ -414,7 +463,8 @@ static int or_fluid_pencil(const or_problem *P, double *const *q, int d, long a,
      * from predicted cells e-1 .. e+2 (eq0230) */
     for (e = OR_NG - 1; e < OR_NG + n; ++e) {
         double F[5];
-        or_flux2(P, &S->c1[e - 1], &S->c1[e], &S->c1[e + 1], &S->c1[e + 2], &ph[e - 1], F);
+        or_flux2(P, &S->c1[e - 1], &S->c1[e], &S->c1[e + 1], &S->c1[e + 2], &ph[e - 1],
+                 nu ? &dw[e - 1] : NULL, F);
         for (k = 0; k < 5; ++k) S->F2[k * m + e] = F[k];
     }
 
@@ -422,10 +472,11 @@ static int or_fluid_pencil(const or_problem *P, double *const *q, int d, long a,
     for (e = OR_NG; e < OR_NG + n; ++e) {
         double un[5];
         long idx = or_index_dir(P, d, e - OR_NG, a, b);
+        const double he = nu ? dw[e] : hd;
         for (k = 0; k < 5; ++k)
-            un[k] = u[k * m + e] - dt / hd * (S->F2[k * m + e] - S->F2[k * m + e - 1]);
+            un[k] = u[k * m + e] - dt / he * (S->F2[k * m + e] - S->F2[k * m + e - 1]);
         if (grav) {
-            double dphi = (ph[e + 1] - ph[e - 1]) / (2.0 * hd);
+            double dphi = (ph[e + 1] - ph[e - 1]) / or_centre_span(P, d, e - OR_NG);
             un[1] = un[1] - dt * S->up[0 * m + e] * dphi;
             un[4] = un[4] - dt * S->up[1 * m + e] * dphi;
         }
@@ -449,6 +500,15 @@ static int or_fluid_pencil(const or_problem *P, double *const *q, int d, long a,
  * Steps: face velocity (eq0361-eq0362), edge velocity (eq0364), upwind
  * first-order flux of the cell products (eq0363, reading C-7), predictor
  * half step, TVD corrector flux with the fluid's limiter (reading C-10). */
+/* Edge velocity at the interface between pencil cells e and e+1 (eq0364):
+ * the mean of the two smoothed face velocities, or on an irregular mesh
+ * their linear interpolation to the interface (reading C-27). */
+static double or_edge_velocity(int nu, double va, double vb, double wa, double wb)
+{
+    if (!nu) return 0.5 * (va + vb);
+    return (wb * va + wa * vb) / (wa + wb);
+}
+
 static void or_ct_face_pencil(const or_problem *P, double *const *q, int d, int c, long fc,
                               long fo, double dt, or_scratch *S, double *f)
 {
@@ -456,9 +516,15 @@ static void or_ct_face_pencil(const or_problem *P, double *const *q, int d, int 
     const long m = n + 2 * OR_NG;
     const int o = 3 - d - c; /* the remaining axis */
     const double hd = P->h[d];
+    const int nu = P->w[d] != NULL;
     double *vt = S->vt, *bf = S->bf, *vh = S->vh, *w = S->w, *f1 = S->f1, *bp = S->bp,
-           *wp = S->wp, *f2 = S->f2;
+           *wp = S->wp, *f2 = S->f2, *dw = S->dw;
+    /* irregular mesh along c: the face velocity is the linear interpolation
+     * of the two cell velocities to the face (reading C-27) */
+    const double wA = or_width(P, c, fc), wB = or_width(P, c, fc + 1);
     long e;
+
+    for (e = 0; e < m; ++e) dw[e] = or_width(P, d, e - OR_NG);
 
     for (e = 0; e < m; ++e) {
         long s = e - OR_NG, cA[3], cB[3], iA, iB, iF;
@@ -468,7 +534,10 @@ static void or_ct_face_pencil(const or_problem *P, double *const *q, int d, int 
         iA = or_index(P, cA[0], cA[1], cA[2]);
         iB = or_index(P, cB[0], cB[1], cB[2]);
         iF = iA; /* the face fc+1/2 is stored at cell index fc (mapped) */
-        vt[e] = 0.5 * (q[1 + d][iA] / q[0][iA] + q[1 + d][iB] / q[0][iB]); /* eq0361 */
+        if (!P->w[c])
+            vt[e] = 0.5 * (q[1 + d][iA] / q[0][iA] + q[1 + d][iB] / q[0][iB]); /* eq0361 */
+        else
+            vt[e] = (wB * (q[1 + d][iA] / q[0][iA]) + wA * (q[1 + d][iB] / q[0][iB])) / (wA + wB);
         bf[e] = q[5 + c][iF];
     }
     for (e = 1; e + 1 < m; ++e)
@@ -476,11 +545,11 @@ static void or_ct_face_pencil(const or_problem *P, double *const *q, int d, int 
     for (e = 1; e + 1 < m; ++e) w[e] = vh[e] * bf[e];
     /* predictor: first-order upwind fluxes at (e, e+1), e = 1 .. m-3 */
     for (e = 1; e + 2 < m; ++e) {
-        double vbar = 0.5 * (vh[e] + vh[e + 1]);                  /* eq0364 */
+        double vbar = or_edge_velocity(nu, vh[e], vh[e + 1], dw[e], dw[e + 1]);  /* eq0364 */
         f1[e] = vbar > 0.0 ? w[e] : w[e + 1];                     /* eq0363 */
     }
     for (e = 2; e + 2 < m; ++e) {
-        bp[e] = bf[e] - dt / (2.0 * hd) * (f1[e] - f1[e - 1]);
+        bp[e] = bf[e] - dt / (2.0 * (nu ? dw[e] : hd)) * (f1[e] - f1[e - 1]);
         wp[e] = vh[e] * bp[e];
     }
     /* corrector: piecewise-linear TVD flux about the upwind cell; the hybrid
@@ -489,11 +558,23 @@ static void or_ct_face_pencil(const or_problem *P, double *const *q, int d, int 
     {
         const int lim = P->limiter == OR_LIM_HYBRID ? OR_LIM_VANLEER : P->limiter;
         for (e = OR_NG - 1; e < OR_NG + n; ++e) {
-            double vbar = 0.5 * (vh[e] + vh[e + 1]);
-            if (vbar > 0.0)
-                f2[e] = wp[e] + 0.5 * or_limit(lim, wp[e] - wp[e - 1], wp[e + 1] - wp[e]);
-            else
-                f2[e] = wp[e + 1] - 0.5 * or_limit(lim, wp[e + 1] - wp[e], wp[e + 2] - wp[e + 1]);
+            double vbar = or_edge_velocity(nu, vh[e], vh[e + 1], dw[e], dw[e + 1]);
+            if (!nu) {
+                if (vbar > 0.0)
+                    f2[e] = wp[e] + 0.5 * or_limit(lim, wp[e] - wp[e - 1], wp[e + 1] - wp[e]);
+                else
+                    f2[e] = wp[e + 1] - 0.5 * or_limit(lim, wp[e + 1] - wp[e], wp[e + 2] - wp[e + 1]);
+            } else {
+                /* slopes per unit length over the centre distances, carried
+                 * over half the upwind cell (reading C-25) */
+                const double gl = 0.5 * (dw[e - 1] + dw[e]), gc = 0.5 * (dw[e] + dw[e + 1]),
+                             gr = 0.5 * (dw[e + 1] + dw[e + 2]);
+                if (vbar > 0.0)
+                    f2[e] = wp[e] + 0.5 * dw[e] * or_limit(lim, (wp[e] - wp[e - 1]) / gl, (wp[e + 1] - wp[e]) / gc);
+                else
+                    f2[e] = wp[e + 1] - 0.5 * dw[e + 1] *
+                            or_limit(lim, (wp[e + 1] - wp[e]) / gc, (wp[e + 2] - wp[e + 1]) / gr);
+            }
         }
     }
     for (e = -1; e < n; ++e) f[e + 1] = f2[e + OR_NG];
@@ -560,10 +641,14 @@ static int or_ct_sweep(const or_problem *P, double *const *q, int d, double dt)
             for (s = 0; s < n; ++s) {
                 long idx = or_index_dir(P, d, s, a, b);
                 /* f[s+1] is the flux at interface s' */
-                nb[t1][idx] = q[5 + t1][idx] - dt / P->h[d] * (fa[s + 1] - fa[s]);
-                nb[t2][idx] = q[5 + t2][idx] - dt / P->h[d] * (fb[s + 1] - fb[s]);
-                nb[d][idx] = q[5 + d][idx] + dt / P->h[t1] * (fa[s + 1] - fam[s + 1])
-                                           + dt / P->h[t2] * (fb[s + 1] - fbm[s + 1]);
+                /* eq037 on the faces: the width of the cell a face pencil
+                 * crosses along d, and for b_d the widths of its cell
+                 * along t1 and t2 */
+                const double hs = or_width(P, d, s), ha = or_width(P, t1, a), hb = or_width(P, t2, b);
+                nb[t1][idx] = q[5 + t1][idx] - dt / hs * (fa[s + 1] - fa[s]);
+                nb[t2][idx] = q[5 + t2][idx] - dt / hs * (fb[s + 1] - fb[s]);
+                nb[d][idx] = q[5 + d][idx] + dt / ha * (fa[s + 1] - fam[s + 1])
+                                           + dt / hb * (fb[s + 1] - fbm[s + 1]);
             }
         }
     for (ax = 0; ax < 3; ++ax) {
@@ -607,7 +692,7 @@ static void or_gravity(const or_problem *P, double *const *q, int d, double tau)
         cp[d] += 1;
         cm[d] -= 1;
         dphi = (P->phi[or_index(P, cp[0], cp[1], cp[2])] - P->phi[or_index(P, cm[0], cm[1], cm[2])]) /
-               (2.0 * P->h[d]);
+               or_centre_span(P, d, c[d]);
         rho = q[0][idx];
         mo = q[1 + d][idx];
         mn = mo - tau * rho * dphi;
@@ -704,7 +789,7 @@ double oracle_cfl(const or_problem *P, const double *state, double k)
             or_cell ce;
             double r;
             or_cell_eval(P, ue, be, &ce, &fl);
-            r = P->h[d] / (fabs(ce.vn) + ce.cf);
+            r = or_width(P, d, c[d]) / (fabs(ce.vn) + ce.cf);   /* eq0420 */
             if (r < best) best = r;
         }
     }
@@ -720,6 +805,7 @@ void oracle_diag(const or_problem *P, const double *state, double *out)
     const long nx = P->n[0], ny = P->n[1], nz = P->n[2];
     const long N = nx * ny * nz;
     const double vol = P->h[0] * P->h[1] * P->h[2];
+    const int nu = P->w[0] || P->w[1] || P->w[2];
     const double *q[8];
     double mx = 0.0;
     long f, i, j, k;
@@ -727,8 +813,17 @@ void oracle_diag(const or_problem *P, const double *state, double *out)
     for (f = 0; f < 8; ++f) {
         double s = 0.0;
         long idx;
-        for (idx = 0; idx < N; ++idx) s += q[f][idx];
-        out[f] = s * vol;
+        if (!nu) {
+            for (idx = 0; idx < N; ++idx) s += q[f][idx];
+            out[f] = s * vol;
+        } else {
+            /* irregular mesh: each cell weighted by its own volume */
+            for (idx = 0; idx < N; ++idx) {
+                long ii = idx % nx, jj = (idx / nx) % ny, kk = idx / (nx * ny);
+                s += q[f][idx] * (or_width(P, 0, ii) * or_width(P, 1, jj) * or_width(P, 2, kk));
+            }
+            out[f] = s;
+        }
     }
     for (k = 0; k < nz; ++k)
         for (j = 0; j < ny; ++j)
@@ -738,9 +833,9 @@ void oracle_diag(const or_problem *P, const double *state, double *out)
                 if (P->bc == OR_BC_OUTFLOW &&
                     ((nx > 1 && i == 0) || (ny > 1 && j == 0) || (nz > 1 && k == 0)))
                     continue;
-                dv = (q[5][idx] - q[5][or_index(P, i - 1, j, k)]) / P->h[0]
-                   + (q[6][idx] - q[6][or_index(P, i, j - 1, k)]) / P->h[1]
-                   + (q[7][idx] - q[7][or_index(P, i, j, k - 1)]) / P->h[2];
+                dv = (q[5][idx] - q[5][or_index(P, i - 1, j, k)]) / or_width(P, 0, i)
+                   + (q[6][idx] - q[6][or_index(P, i, j - 1, k)]) / or_width(P, 1, j)
+                   + (q[7][idx] - q[7][or_index(P, i, j, k - 1)]) / or_width(P, 2, k);
                 if (fabs(dv) > mx) mx = fabs(dv);
             }
     out[8] = mx;

@@ -602,29 +602,45 @@ template <class T> struct TransArgs {
     long long plane;     // elements per z-plane
 };
 
+// Tiles of 64 source rows x 32 elements: a thread keeps eight loads in
+// flight, and the loads of field f+1 are issued before field f is stored
+// (two tiles, one barrier per field: a tile is rewritten two fields later,
+// after every thread has passed the barrier between).
 template <class T>
 __global__ void __launch_bounds__(256) transpose_kernel(TransArgs<T> A)
 {
-    __shared__ T tile[32][33];
-    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+    __shared__ T tile[2][64][33];
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 64;
     const long long zoff = (long long)blockIdx.z * A.plane;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    const int rl = r0 + tx;
+    T v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int c = c0 + ty + 8 * k;
+        v[k] = (rl < A.nr && c < A.nc) ? A.src[0][zoff + (long long)c * A.nr + rl] : T(0);
+    }
 #pragma unroll 1
     for (int f = 0; f < A.nf; ++f) {
-        const T *__restrict__ src = A.src[f] + zoff;
+        const int b = f & 1;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) tile[b][ty + 8 * k][tx] = v[k];
+        __syncthreads();
+        if (f + 1 < A.nf) {
+            const T *__restrict__ src = A.src[f + 1] + zoff;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int c = c0 + ty + 8 * k;
+                v[k] = (rl < A.nr && c < A.nc) ? src[(long long)c * A.nr + rl] : T(0);
+            }
+        }
         T *__restrict__ dst = A.dst[f] + zoff;
 #pragma unroll
-        for (int k = 0; k < 32; k += 8) {
-            const int r = r0 + tx, c = c0 + ty + k;
-            if (r < A.nr && c < A.nc) tile[ty + k][tx] = src[(long long)c * A.nr + r];
+        for (int k = 0; k < 8; ++k) {
+            const int idx = ty + 8 * k;  // 0 .. 63: destination row r0 + (idx & 31), column half idx >> 5
+            const int r = r0 + (idx & 31), cl = tx + 32 * (idx >> 5), c = c0 + cl;
+            if (r < A.nr && c < A.nc) dst[(long long)r * A.nc + c] = tile[b][cl][idx & 31];
         }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < 32; k += 8) {
-            const int c = c0 + tx, r = r0 + ty + k;
-            if (r < A.nr && c < A.nc) dst[(long long)r * A.nc + c] = tile[tx][ty + k];
-        }
-        __syncthreads();
     }
 }
 

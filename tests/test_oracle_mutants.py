@@ -22,14 +22,23 @@ MUTANTS = {
     "ct_bz_sign_as_printed": ("nb[t2][idx] = q[5 + t2][idx] - dt", "nb[t2][idx] = q[5 + t2][idx] + dt"),
     "ct_constraint_index": ("(fa[s + 1] - fam[s + 1])", "(fa[s + 1] - fam[s])"),
     "ct_face_neighbour": ("cB[d] = s; cB[c] = fc + 1; cB[o] = fo;", "cB[d] = s; cB[c] = fc - 1; cB[o] = fo;"),
-    "minus_slope_sign": ("double slm = or_limit(lim, fm2 - fm1, fm3 - fm2);   /* eq0220 */",
-                         "double slm = or_limit(lim, fm1 - fm2, fm3 - fm2);   /* eq0220 */"),
+    "minus_slope_sign": ("slm = or_limit(lim, fm2 - fm1, fm3 - fm2);   /* eq0220 */",
+                         "slm = or_limit(lim, fm1 - fm2, fm3 - fm2);   /* eq0220 */"),
     "hybrid_criterion_inverted": ("? OR_LIM_MINMOD : OR_LIM_VANLEER;", "? OR_LIM_VANLEER : OR_LIM_MINMOD;"),
     "split_gravity_sign": ("mn = mo - tau * rho * dphi;", "mn = mo + tau * rho * dphi;"),
+    "nu_slope_width_other_side": ("        sp = dw[1];\n", "        sp = dw[2];\n"),
+    "nu_update_neighbour_width": ("        const double he = nu ? dw[e] : hd;\n        for (k = 0; k < 5; ++k)\n            un[k]",
+                                  "        const double he = nu ? dw[e + 1] : hd;\n        for (k = 0; k < 5; ++k)\n            un[k]"),
+    "nu_centre_span_own_width": ("    return 0.5 * or_width(P, d, s - 1) + or_width(P, d, s) + 0.5 * or_width(P, d, s + 1);",
+                                 "    return 2.0 * or_width(P, d, s);"),
+    "nu_face_velocity_weights_swapped": ("vt[e] = (wB * (q[1 + d][iA] / q[0][iA]) + wA * (q[1 + d][iB] / q[0][iB])) / (wA + wB);",
+                                         "vt[e] = (wA * (q[1 + d][iA] / q[0][iA]) + wB * (q[1 + d][iB] / q[0][iB])) / (wA + wB);"),
+    "nu_constraint_width": ("ha = or_width(P, t1, a),", "ha = or_width(P, t1, a + 1),"),
+    "nu_ct_corrector_width": ("f2[e] = wp[e] + 0.5 * dw[e] * or_limit", "f2[e] = wp[e] + 0.5 * dw[e + 1] * or_limit"),
     "split_gravity_energy_dropped": ("q[4][idx] = q[4][idx] + 0.5 * (mn * mn - mo * mo) / rho;", "(void)mo;"),
     "slopes_added": ("F[k] = fp1 + fm2 + 0.5 * (slp - slm);", "F[k] = fp1 + fm2 + 0.5 * (slp + slm);"),
     "freezing_speed_wrong_interface": ("double D = fmax(c1->d, c2->d);", "double D = fmax(c0->d, c1->d);"),
-    "predictor_full_step": ("up[k] = u[k * m + e] - dt / (2.0 * hd) *", "up[k] = u[k * m + e] - dt / hd *"),
+    "predictor_full_step": ("up[k] = u[k * m + e] - dt / (2.0 * he) *", "up[k] = u[k * m + e] - dt / he *"),
     "gravity_sign": ("up[1] = up[1] - 0.5 * dt * u[0 * m + e] * dphi;", "up[1] = up[1] + 0.5 * dt * u[0 * m + e] * dphi;"),
     "corrector_source_old_state": ("un[4] = un[4] - dt * S->up[1 * m + e] * dphi;", "un[4] = un[4] - dt * u[1 * m + e] * dphi;"),
     "pressure_drops_magnetic": ("p = (g - 1.0) * (u[4] - kin - mag);", "p = (g - 1.0) * (u[4] - kin);"),
@@ -208,11 +217,75 @@ def battery(oracle_mod, lib):
                 and np.allclose(ob.state[4, 0, 0, s], p / (2 / 3) + 0.5 * (rho * g * dt) ** 2 / rho,
                                 rtol=1e-13, atol=0))
 
+    def nu_uniform():
+        from test_oracle_pins import nu_box
+        w = W.random_smooth(10, 9, 8, seed=61, h=(0.1, 0.11, 0.125))
+        a = _box(oracle_mod, lib, w)
+        b = oracle_mod.OracleBox(*w.dims, w.gamma, bc=w.bc, h=w.h, lib=lib,
+                                 widths=[np.full(n, h) for n, h in zip(w.dims, w.h)])
+        b.set_state(w.state)
+        dt = a.cfl(0.5)
+        a.step(dt, 2)
+        b.step(dt, 2)
+        return np.max(np.abs(a.state - b.state)) <= 1e-13 * np.max(np.abs(a.state))
+
+    def nu_conserve():
+        from test_oracle_pins import stretched, nu_divergence
+        w = W.random_smooth(12, 10, 9, seed=62)
+        widths = [stretched(12, phase=0.3), stretched(10, amp=0.4, phase=1.1), stretched(9, amp=0.25, phase=2.0)]
+        ob = oracle_mod.OracleBox(*w.dims, w.gamma, bc=w.bc, h=w.h, lib=lib, widths=widths)
+        ob.set_state(w.state)
+        d0 = ob.diag()
+        div0 = nu_divergence(ob)
+        ob.step(ob.cfl(0.5), 2)
+        d1 = ob.diag()
+        vol = widths[0][None, None, :] * widths[1][None, :, None] * widths[2][:, None, None]
+        scale = np.array([np.sum(np.abs(ob.state[f]) * vol) for f in range(8)])
+        div1 = nu_divergence(ob)
+        return (np.all(np.abs(d1[:8] - d0[:8]) <= 1e-13 * scale)
+                and np.max(np.abs(div1 - div0)) * 0.05 / np.max(np.abs(ob.state[5:8])) < 1e-13)
+
+    def nu_mirror():
+        from test_oracle_pins import stretched, _mirror_x
+        w = W.random_smooth(16, 7, 6, seed=63)
+        wx = stretched(16, amp=0.45, phase=0.7)
+        wy, wz = stretched(7, amp=0.3), stretched(6, amp=0.2, phase=0.5)
+        a = oracle_mod.OracleBox(*w.dims, w.gamma, bc=w.bc, h=w.h, lib=lib, widths=[wx, wy, wz])
+        a.set_state(w.state)
+        b = oracle_mod.OracleBox(*w.dims, w.gamma, bc=w.bc, h=w.h, lib=lib, widths=[wx[::-1], wy, wz])
+        b.set_state(_mirror_x(w.state))
+        dt = a.cfl(0.5)
+        a.step(dt, 2)
+        b.step(dt, 2)
+        return np.max(np.abs(_mirror_x(a.state) - b.state)) <= 1e-13 * np.max(np.abs(a.state))
+
+    def nu_freefall():
+        from test_oracle_pins import stretched, centres
+        n, g, rho, p = 24, 0.7, 1.3, 2.0
+        wx = stretched(n, amp=0.5)
+        shape = (1, 1, n)
+        st = W.assemble(np.full(shape, rho), (0.0, 0.0, 0.0), p, (0.0, 0.0, 0.0), 5 / 3, W.BC_OUTFLOW)
+        phi = np.broadcast_to(g * centres(wx), shape).copy()
+        ok = True
+        for split in (False, True):
+            ob = oracle_mod.OracleBox(n, 1, 1, 5 / 3, bc=W.BC_OUTFLOW, h=(1.0 / n, 1, 1), phi=phi, lib=lib,
+                                      widths=[wx, None, None], gravity_split=split)
+            ob.set_state(st)
+            ob.fluid(0, 0.004)
+            ok = ok and np.allclose(ob.state[1, 0, 0, 4:n - 4], -rho * g * 0.004, rtol=1e-12, atol=0)
+        return ok
+
+    def nu_face_velocity():
+        from test_oracle_pins import face_velocity_case
+        return face_velocity_case(oracle_mod, lib)
+
     for name, fn in [("alfven", alfven), ("oblique", oblique), ("fastwave", fastwave),
                      ("entropy", entropy), ("sod", sod),
                      ("invariants", invariants), ("freefall", freefall), ("cfl", cfl),
                      ("atmosphere", atmosphere), ("rusanov", rusanov), ("uniform", uniform),
-                     ("hybrid", hybrid), ("splitfall", splitfall)]:
+                     ("hybrid", hybrid), ("splitfall", splitfall), ("nu_uniform", nu_uniform),
+                     ("nu_conserve", nu_conserve), ("nu_mirror", nu_mirror), ("nu_freefall", nu_freefall),
+                     ("nu_face_velocity", nu_face_velocity)]:
         try:
             with np.errstate(all="ignore"):
                 ok = bool(fn())

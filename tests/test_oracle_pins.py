@@ -483,3 +483,169 @@ def test_split_gravity_free_fall(oracle_mod):
     ou.set_state(st)
     ou.step(dt)
     assert not np.array_equal(ou.state, ob.state)
+
+
+# ---------------------------------------------------------------------------
+# irregular Cartesian meshes (Sec. 2.5, eq037, eq0420; readings C-23 .. C-27)
+# ---------------------------------------------------------------------------
+
+def stretched(n, L=1.0, amp=0.3, phase=0.0):
+    """Smoothly varying positive cell widths summing to L (periodic in i)."""
+    x = (np.arange(n) + 0.5) / n
+    w = 1.0 + amp * np.sin(2 * np.pi * x + phase)
+    return L * w / w.sum()
+
+
+def centres(w):
+    return np.cumsum(w) - 0.5 * w
+
+
+def nu_box(oracle_mod, w, widths, **kw):
+    ob = oracle_mod.OracleBox(*w.dims, w.gamma, bc=w.bc, h=w.h, phi=w.phi, widths=widths, **kw)
+    ob.set_state(w.state)
+    return ob
+
+
+def nu_divergence(ob):
+    b = ob.state[5:8]
+    wx, wy, wz = (ob.widths[d] if ob.widths[d] is not None else np.full(ob.n[d], ob.h[d]) for d in range(3))
+    return ((b[0] - np.roll(b[0], 1, 2)) / wx[None, None, :] + (b[1] - np.roll(b[1], 1, 1)) / wy[None, :, None]
+            + (b[2] - np.roll(b[2], 1, 0)) / wz[:, None, None])
+
+
+def test_irregular_mesh_with_uniform_widths_is_the_uniform_method(oracle_mod):
+    """Width arrays that are all equal give the printed uniform-mesh method
+    up to rounding (the per-length slopes times half a width reduce to
+    eq0230, the centre span to 2h)."""
+    w = W.random_smooth(10, 9, 8, seed=61, h=(0.1, 0.11, 0.125))
+    phi = 0.3 * np.sin(2 * np.pi * np.arange(10) / 10)[None, None, :] * np.ones((8, 9, 10))
+    w = W.Workload("r", w.state, w.gamma, w.h, w.bc, phi=phi)
+    for lim in (0, 1, 3):
+        a = make_box(oracle_mod, w, limiter=lim)
+        b = nu_box(oracle_mod, w, [np.full(n, h) for n, h in zip(w.dims, w.h)], limiter=lim)
+        dt = a.cfl(0.5)
+        assert abs(b.cfl(0.5) - dt) <= 1e-15 * dt
+        a.step(dt, 2)
+        b.step(dt, 2)
+        assert np.max(np.abs(a.state - b.state)) <= 1e-13 * np.max(np.abs(a.state))
+
+
+@pytest.mark.parametrize("lim", [0, 1])
+def test_irregular_mesh_conservation_and_divergence(oracle_mod, lim):
+    """Periodic box stretched along every axis: the volume-weighted totals of
+    all eight fields (sum u_ijk dx_i dy_j dz_k) and the discrete divergence
+    with per-cell widths are kept to round-off (eq037 in flux form)."""
+    w = W.random_smooth(12, 10, 9, seed=62)
+    widths = [stretched(12, phase=0.3), stretched(10, amp=0.4, phase=1.1), stretched(9, amp=0.25, phase=2.0)]
+    ob = nu_box(oracle_mod, w, widths, limiter=lim)
+    d0 = ob.diag()
+    div0 = nu_divergence(ob)
+    ob.step(ob.cfl(0.5), 3)
+    d1 = ob.diag()
+    vol = widths[0][None, None, :] * widths[1][None, :, None] * widths[2][:, None, None]
+    scale = np.array([np.sum(np.abs(ob.state[f]) * vol) for f in range(8)])
+    assert np.all(np.abs(d1[:8] - d0[:8]) <= 1e-13 * scale)
+    div1 = nu_divergence(ob)
+    assert np.max(np.abs(div1 - div0)) * min(min(x) for x in widths) / np.max(np.abs(ob.state[5:8])) < 1e-13
+    # the totals really are volume-weighted: plain sums are not conserved
+    assert abs(np.sum(ob.state[0]) - np.sum(w.state[0])) > 1e-9
+
+
+def test_irregular_mesh_uniform_state_is_fixed_point(oracle_mod):
+    st = W.assemble(np.full((5, 6, 7), 1.3), (0.4, -0.2, 0.7), 0.9, (0.3, -0.5, 0.25), 5 / 3, 0)
+    w = W.Workload("u", st, 5 / 3, (0.1, 0.2, 0.3))
+    ob = nu_box(oracle_mod, w, [stretched(7, 0.7), stretched(6, 1.2, 0.4), stretched(5, 1.5, 0.2, 1.0)])
+    ob.step(0.01, 2)
+    assert np.max(np.abs(ob.state - st)) <= 1e-14 * np.max(np.abs(st))
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_irregular_mesh_free_fall(oracle_mod, split):
+    """Uniform gas at rest in phi = g x on a stretched outflow mesh: the
+    centred difference over the centre span (reading C-26) is exactly g, so
+    interior cells gain -rho g dt of momentum in one L_x (unsplit source) or
+    one G L G (split), with the internal energy unchanged."""
+    n, g, rho, p, gam = 24, 0.7, 1.3, 2.0, 5.0 / 3.0
+    wx = stretched(n, amp=0.5)
+    x = centres(wx)
+    shape = (1, 1, n)
+    st = W.assemble(np.full(shape, rho), (0.0, 0.0, 0.0), p, (0.0, 0.0, 0.0), gam, W.BC_OUTFLOW)
+    w = W.Workload("ff", st, gam, (1.0 / n, 1, 1), bc=W.BC_OUTFLOW, phi=np.broadcast_to(g * x, shape).copy())
+    ob = nu_box(oracle_mod, w, [wx, None, None], gravity_split=split)
+    dt = 0.004
+    ob.fluid(0, dt)
+    s = slice(4, n - 4)
+    assert np.allclose(ob.state[1, 0, 0, s], -rho * g * dt, rtol=1e-12, atol=0)
+    eint = ob.state[4, 0, 0, s] - 0.5 * ob.state[1, 0, 0, s] ** 2 / rho
+    assert np.allclose(eint, p / (gam - 1), rtol=1e-12, atol=0)
+
+
+def _mirror_x(st):
+    """Reflection x -> -x of a state periodic in x: cells reversed, v_x and
+    b_x change sign, b_x faces i+1/2 map to faces (n-2-i)+1/2."""
+    out = st[..., ::-1].copy()
+    out[1] = -out[1]
+    out[5] = -np.roll(out[5], -1, axis=-1)
+    return out
+
+
+def test_irregular_mesh_mirror_symmetry(oracle_mod):
+    """The method on a stretched mesh commutes with a reflection of state and
+    mesh: catches a width taken from the wrong side of an interface."""
+    w = W.random_smooth(16, 7, 6, seed=63)
+    wx = stretched(16, amp=0.45, phase=0.7)
+    wy, wz = stretched(7, amp=0.3), stretched(6, amp=0.2, phase=0.5)
+    a = nu_box(oracle_mod, w, [wx, wy, wz])
+    b = nu_box(oracle_mod, W.Workload("m", _mirror_x(w.state), w.gamma, w.h), [wx[::-1], wy, wz])
+    dt = a.cfl(0.5)
+    assert abs(b.cfl(0.5) - dt) <= 1e-15 * dt
+    a.step(dt, 2)
+    b.step(dt, 2)
+    assert np.max(np.abs(_mirror_x(a.state) - b.state)) <= 1e-13 * np.max(np.abs(a.state))
+
+
+def test_irregular_mesh_cfl_closed_form(oracle_mod):
+    """eq0420: dt = k min over cells and axes of width / (|v_d| + c_F,d)."""
+    gam, rho, p, B = 5 / 3, 2.0, 0.6, 1.1
+    a2, va2 = gam * p / rho, B * B / rho
+    v = (0.3, -0.2, 0.1)
+    one = np.ones((3, 4, 5))
+    st = W.assemble(rho * one, tuple(c * one for c in v), p, (B * one, 0 * one, 0 * one), gam, 0)
+    widths = [stretched(5, 0.5, 0.4), stretched(4, 0.7, 0.3), stretched(3, 0.9, 0.2)]
+    ob = nu_box(oracle_mod, W.Workload("c", st, gam, (0.1, 0.2, 0.3)), widths)
+    cf = [max(math.sqrt(a2), math.sqrt(va2)), math.sqrt(a2 + va2), math.sqrt(a2 + va2)]
+    ref = 0.8 * min(widths[d].min() / (abs(v[d]) + cf[d]) for d in range(3))
+    assert abs(ob.cfl(0.8) - ref) < 1e-14 * ref
+
+
+def face_velocity_case(oracle_mod, lib=None):
+    """B_x on a shear flow v_x = U + s y (uniform in x) with b_y = b_y(x) on
+    a mesh stretched along y: the face velocity interpolated linearly to
+    the face y_{j+1/2} (reading C-27) is exactly U + s y_{j+1/2}, so each
+    interior face pencil of b_y evolves as under the uniform velocity of its
+    face.  True when every interior face matches to round-off."""
+    nx, ny, U, s, dt = 16, 8, 0.3, 1.7, 0.01
+    wy = stretched(ny, amp=0.5, phase=0.9)
+    yc, yf = centres(wy), np.cumsum(wy)
+    x = (np.arange(nx) + 0.5) / nx
+    by = np.broadcast_to(0.2 + 0.1 * np.sin(2 * np.pi * x)[None, None, :], (1, ny, nx)).copy()
+    zero = np.zeros((1, ny, nx))
+    vx = np.broadcast_to((U + s * yc)[None, :, None], (1, ny, nx)).copy()
+
+    def run(v):
+        st = W.assemble(np.ones((1, ny, nx)), (v, zero, zero), 1.0, (zero, by, zero), 5 / 3, 0)
+        ob = oracle_mod.OracleBox(nx, ny, 1, 5 / 3, lib=lib, widths=[None, wy, None])
+        ob.set_state(st)
+        ob.ct(0, dt)
+        return ob.state[6, 0]
+
+    got = run(vx)
+    ok = True
+    for j in range(ny - 1):
+        ref = run(np.full((1, ny, nx), U + s * yf[j]))
+        ok = ok and np.max(np.abs(got[j] - ref[j])) <= 1e-13
+    return ok
+
+
+def test_irregular_mesh_face_velocity_interpolation(oracle_mod):
+    assert face_velocity_case(oracle_mod)
