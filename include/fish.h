@@ -116,8 +116,23 @@ int fish_set_state_device(fish_ctx *ctx, const void *state, int dtype);
 int fish_set_state_host(fish_ctx *ctx, const void *state, int dtype);
 
 /* Fixed cell-centred potential phi (nx*ny*nz doubles, host) for the unsplit
- * gravity source (eq0253-eq0255); NULL removes gravity. */
+ * gravity source (eq0253-eq0255) or the split operator of FISH_OPT_GRAVITY;
+ * NULL removes gravity. */
 int fish_set_potential(fish_ctx *ctx, const double *phi);
+
+/* Irregular Cartesian mesh (Sec. 2.5, eq037, eq0420): host arrays of nx, ny,
+ * nz cell widths (each finite and > 0; copied, the caller keeps ownership).
+ * A NULL axis keeps the width of FISH_OPT_DX/DY/DZ for all its cells; all
+ * three NULL restores the uniform mesh.  With a mesh set, every update uses
+ * the width of the cell it changes, the TVD slopes are per unit length over
+ * the centre distances, potential differences are taken over the centre
+ * span, CT face and edge velocities are linear interpolations, the CFL step
+ * follows eq0420 and fish_diagnostics weights each cell by its own volume.
+ * Ghost cells have the width of the cell they copy.  The one-column kernels
+ * run every sweep (no packed FP32x2 path, no CFL fused into the last sweep).
+ * Widths are uploaded at the next stepping call.  FISH_ERR_ARG on a bad
+ * width. */
+int fish_set_mesh(fish_ctx *ctx, const double *dx, const double *dy, const double *dz);
 
 /* CFL time step dt = k * min over cells and axes d of h_d / (|v_d| + c_F,d)
  * (eq0083-eq0084, reading C-15) for the current state.  Synchronises. */

@@ -32,7 +32,7 @@ FISH_BATCH_OPT_LIMITER, FISH_BATCH_OPT_ORDER, FISH_BATCH_OPT_GROUPS, FISH_BATCH_
 
 # every symbol include/fish.h declares (checked by the CPU test suite)
 EXPORTS = ("fish_create", "fish_set_option", "fish_set_stream", "fish_set_allocator", "fish_set_state",
-           "fish_set_state_device", "fish_set_state_host", "fish_set_potential", "fish_cfl_dt", "fish_step", "fish_step_cfl",
+           "fish_set_state_device", "fish_set_state_host", "fish_set_potential", "fish_set_mesh", "fish_cfl_dt", "fish_step", "fish_step_cfl",
            "fish_last_dt", "fish_apply", "fish_get_state", "fish_get_state_device", "fish_diagnostics",
            "fish_sync", "fish_clear_error", "fish_last_error", "fish_launch_count", "fish_destroy",
            "fish_diagnostics_noalloc", "fish_batch_create", "fish_batch_set_option", "fish_batch_set_stream",
@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH):
             "fish_set_state_device": ([P, P, ctypes.c_int], ctypes.c_int),
             "fish_set_state_host": ([P, P, ctypes.c_int], ctypes.c_int),
             "fish_set_potential": ([P, D], ctypes.c_int),
+            "fish_set_mesh": ([P, D, D, D], ctypes.c_int),
             "fish_cfl_dt": ([P, ctypes.c_double, D], ctypes.c_int),
             "fish_step": ([P, ctypes.c_double], ctypes.c_int),
             "fish_step_cfl": ([P, ctypes.c_double, ctypes.c_int], ctypes.c_int),
@@ -250,6 +251,22 @@ class Box:
         if a.size != np.prod(self.n):
             raise ValueError("potential has the wrong size")
         self._check(self._lib.fish_set_potential(self.ctx, _dptr(a)), "fish_set_potential")
+
+    def set_mesh(self, widths):
+        """Irregular Cartesian mesh: widths = (dx, dy, dz), each None (the
+        uniform width of that axis) or an array of the axis' cell widths;
+        None restores the uniform mesh."""
+        arrs = [None, None, None]
+        if widths is not None:
+            for d, wd in enumerate(widths):
+                if wd is not None:
+                    a = np.ascontiguousarray(wd, dtype=np.float64).reshape(-1)
+                    if a.size != self.n[d]:
+                        raise ValueError("widths[%d] needs %d entries" % (d, self.n[d]))
+                    arrs[d] = a
+        self._mesh = arrs  # keep the host arrays alive for the call
+        self._check(self._lib.fish_set_mesh(self.ctx, *[None if a is None else _dptr(a) for a in arrs]),
+                    "fish_set_mesh")
 
     def cfl_dt(self, k):
         out = ctypes.c_double()

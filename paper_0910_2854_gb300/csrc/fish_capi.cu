@@ -52,6 +52,14 @@ struct fish_ctx {
     void *phiD[3] = {};    // FP32: phi(next cell along d) - phi(cell) formed in FP64, in the layout of the d sweeps
     bool has_phi = false;
 
+    // irregular Cartesian mesh (eq037): host widths per axis (empty: h of
+    // the axis), device copies of all three in the state's precision
+    bool nu = false;
+    std::vector<double> wmesh[3];
+    void *wdev[3] = {};
+    int wdev_prec = -1;
+    bool mesh_dirty = false;
+
     double *dt_dev = nullptr;       // time step read by the sweep kernels
     double *dt_last = nullptr;      // dt of the last step
     unsigned long long *minbits = nullptr;
@@ -243,12 +251,26 @@ template <class T> const T *sweep_potential(const fish_ctx *c, int d)
     return (const T *)(c->layout ? c->phiT : c->phi);
 }
 
+// Device cell widths of the three axes (irregular mesh), else nullptr.
+template <class T> struct MeshPtrs {
+    const T *w[3] = {nullptr, nullptr, nullptr};
+    const T *const *get() const { return w[0] ? w : nullptr; }
+};
+template <class T> MeshPtrs<T> mesh_of(const fish_ctx *c)
+{
+    MeshPtrs<T> m;
+    if (c->nu)
+        for (int a = 0; a < 3; ++a) m.w[a] = (const T *)c->wdev[a];
+    return m;
+}
+
 // G_d(dt/2) in place on the current fluid buffer (operator-split gravity)
 template <class T> int op_gravity(fish_ctx *c, int d)
 {
     T *u[5];
     for (int f = 0; f < 5; ++f) u[f] = (T *)c->fl[c->cu][f];
-    FISH_CK(c, Launch<T>::gravity(u, sweep_potential<T>(c, d), c->dt_dev, 0.5, geom(c), d, c->h[d], c->stream),
+    const MeshPtrs<T> m = mesh_of<T>(c);
+    FISH_CK(c, Launch<T>::gravity(u, sweep_potential<T>(c, d), c->dt_dev, 0.5, geom(c), d, c->h[d], c->stream, m.w[d]),
             "gravity launch");
     c->launches += 1;
     return FISH_OK;
@@ -272,7 +294,7 @@ template <class T> int op_fluid(fish_ctx *c, int d, bool fuse_cfl)
     FISH_CK(c,
             Launch<T>::fluid(in, out, split ? nullptr : sweep_potential<T>(c, d), c->dt_dev,
                              geom(c), d, c->lim, c->hse != 0, c->gamma, c->alpha, c->h, c->flags,
-                             fuse_cfl ? c->minbits : nullptr, c->stream),
+                             fuse_cfl ? c->minbits : nullptr, c->stream, mesh_of<T>(c).get()),
             "fluid sweep launch");
     c->cu = 1 - c->cu;
     c->launches += 1;
@@ -290,7 +312,7 @@ template <class T> int op_ct(fish_ctx *c, int d)
     }
     FISH_CK(c,
             Launch<T>::ct((const T *)c->fl[c->cu][0], (const T *)c->fl[c->cu][1 + d], b, bo, c->dt_dev, geom(c), d,
-                          c->lim, c->h, c->flags, c->stream),
+                          c->lim, c->h, c->flags, c->stream, mesh_of<T>(c).get()),
             "constrained-transport sweep launch");
     c->cb = 1 - c->cb;
     c->launches += 1;
@@ -310,7 +332,7 @@ int apply_op(fish_ctx *c, int op, int d, bool fuse_cfl = false)
 // minimum of the new state (FP32 two-column kernels only).
 bool last_sweep_fuses_cfl(const fish_ctx *c)
 {
-    if (c->prec != FISH_PREC_FP32 || split_gravity(c)) return false;
+    if (c->prec != FISH_PREC_FP32 || split_gravity(c) || c->nu) return false;
     return Launch<float>::fluid_fuses_cfl(geom_of(c, layout_for(0)), 0, c->lim, c->hse != 0);
 }
 
@@ -334,7 +356,8 @@ template <class T> int queue_cfl(fish_ctx *c)
 {
     const T *in[8];
     for (int f = 0; f < 8; ++f) in[f] = (const T *)field_ptr(c, f);
-    FISH_CK(c, Launch<T>::cfl(in, geom(c), c->h, c->gamma, c->minbits, c->flags, c->stream), "cfl launch");
+    FISH_CK(c, Launch<T>::cfl(in, geom(c), c->h, c->gamma, c->minbits, c->flags, c->stream, mesh_of<T>(c).get()),
+            "cfl launch");
     c->launches += 1;
     return FISH_OK;
 }
@@ -356,11 +379,35 @@ int queue_cfl_dt(fish_ctx *c, double k, double *dt_target, double *dt_copy)
     return FISH_OK;
 }
 
+// Upload the cell widths of an irregular mesh (outside any capture): the
+// given widths per axis, h of the axis where none were given.
+int sync_mesh(fish_ctx *c)
+{
+    if (!c->nu || (!c->mesh_dirty && c->wdev_prec == c->prec)) return FISH_OK;
+    const size_t es = esize(c);
+    for (int a = 0; a < 3; ++a) {
+        if (c->wdev_prec != c->prec) c->wdev[a] = nullptr;  // other precision: fresh arrays
+        if (!c->wdev[a] && !(c->wdev[a] = dev_alloc(c, (size_t)c->n[a] * es)))
+            return fail(c, FISH_ERR_OOM, "mesh allocation failed");
+        std::vector<double> wd(c->n[a], c->h[a]);
+        if (!c->wmesh[a].empty()) wd = c->wmesh[a];
+        if (c->prec == FISH_PREC_FP64) {
+            FISH_CK(c, cudaMemcpy(c->wdev[a], wd.data(), wd.size() * sizeof(double), cudaMemcpyHostToDevice), "mesh");
+        } else {
+            std::vector<float> wf(wd.begin(), wd.end());
+            FISH_CK(c, cudaMemcpy(c->wdev[a], wf.data(), wf.size() * sizeof(float), cudaMemcpyHostToDevice), "mesh");
+        }
+    }
+    c->wdev_prec = c->prec;
+    c->mesh_dirty = false;
+    return FISH_OK;
+}
+
 int ready(fish_ctx *c)
 {
     if (!c) return FISH_ERR_ARG;
     if (!c->allocated) return fail(c, FISH_ERR_STATE, "no state set (call fish_set_state first)");
-    return FISH_OK;
+    return sync_mesh(c);
 }
 
 }  // namespace
@@ -432,6 +479,7 @@ int fish_set_option(fish_ctx *c, int key, double v)
     case FISH_OPT_DZ:
         if (!(v > 0.0) || !std::isfinite(v)) return fail(c, FISH_ERR_ARG, "cell width must be > 0");
         c->h[key - FISH_OPT_DX] = v;
+        c->mesh_dirty = true;
         break;
     default:
         return fail(c, FISH_ERR_ARG, "unknown option key");
@@ -606,6 +654,26 @@ int fish_set_potential(fish_ctx *c, const double *phi)
         FISH_CK(c, cudaStreamSynchronize(c->stream), "phi upload");
     }
     c->has_phi = true;
+    return FISH_OK;
+}
+
+int fish_set_mesh(fish_ctx *c, const double *dx, const double *dy, const double *dz)
+{
+    if (!c) return FISH_ERR_ARG;
+    const double *w[3] = {dx, dy, dz};
+    for (int a = 0; a < 3; ++a)
+        if (w[a])
+            for (int i = 0; i < c->n[a]; ++i)
+                if (!(w[a][i] > 0.0) || !std::isfinite(w[a][i]))
+                    return fail(c, FISH_ERR_ARG, "cell widths must be finite and > 0");
+    for (int a = 0; a < 3; ++a) {
+        c->wmesh[a].clear();
+        if (w[a]) c->wmesh[a].assign(w[a], w[a] + c->n[a]);
+    }
+    c->nu = dx || dy || dz;
+    c->mesh_dirty = true;
+    c->gdirty = true;
+    c->cfl_pending = false;
     return FISH_OK;
 }
 
@@ -793,11 +861,13 @@ int fish_diagnostics(fish_ctx *c, double out[9])
     if (c->prec == FISH_PREC_FP64) {
         const double *in[8];
         for (int f = 0; f < 8; ++f) in[f] = (const double *)field_ptr(c, f);
-        FISH_CK(c, Launch<double>::diag(in, g, c->h, c->partial, kDiagBlocks, c->stream), "diag launch");
+        FISH_CK(c, Launch<double>::diag(in, g, c->h, c->partial, kDiagBlocks, c->stream, mesh_of<double>(c).get()),
+                "diag launch");
     } else {
         const float *in[8];
         for (int f = 0; f < 8; ++f) in[f] = (const float *)field_ptr(c, f);
-        FISH_CK(c, Launch<float>::diag(in, g, c->h, c->partial, kDiagBlocks, c->stream), "diag launch");
+        FISH_CK(c, Launch<float>::diag(in, g, c->h, c->partial, kDiagBlocks, c->stream, mesh_of<float>(c).get()),
+                "diag launch");
     }
     c->launches += 1;
     std::vector<double> part((size_t)9 * kDiagBlocks);
@@ -805,7 +875,8 @@ int fish_diagnostics(fish_ctx *c, double out[9])
                                c->stream),
             "diag download");
     FISH_CK(c, cudaStreamSynchronize(c->stream), "diag");
-    const double vol = c->h[0] * c->h[1] * c->h[2];
+    // an irregular mesh weights each cell by its volume in the kernel
+    const double vol = c->nu ? 1.0 : c->h[0] * c->h[1] * c->h[2];
     for (int f = 0; f < 9; ++f) out[f] = 0.0;
     for (int b = 0; b < kDiagBlocks; ++b) {
         for (int f = 0; f < 8; ++f) out[f] += part[(size_t)b * 9 + f];

@@ -14,10 +14,15 @@ static inline unsigned col_grid(long long work, int block)
     return (unsigned)(g < 1 ? 1 : g);
 }
 
-template <class V, bool HSE, bool GRAV, int LIM, bool FT1>
+template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool NU = false>
 static cudaError_t col_fluid_launch(const ColFluidArgs<typename VT<V>::S> &A, cudaStream_t s)
 {
     const long long cols = (long long)(A.nf / VT<V>::W) * A.no;
+    if constexpr (NU) {
+        if (A.cfl_min) return cudaErrorInvalidValue;
+        fluid_col_kernel<V, HSE, GRAV, LIM, FT1, false, true><<<col_grid(cols, 128), 128, 0, s>>>(A);
+        return cudaGetLastError();
+    }
     if constexpr (std::is_same<V, P2>::value && !HSE) {
         if (A.cfl_min) {
             fluid_col_kernel<V, HSE, GRAV, LIM, FT1, true><<<col_grid(cols, 128), 128, 0, s>>>(A);
@@ -33,11 +38,14 @@ template <class V, bool HSE, bool GRAV, bool FT1>
 static cudaError_t col_fluid_lim(const ColFluidArgs<typename VT<V>::S> &A, cudaStream_t s)
 {
     if constexpr (std::is_same<V, P2>::value) {
-        // compile-time limiters for the throughput path
+        // compile-time limiters for the throughput path (uniform meshes only)
+        if (A.wd) return cudaErrorInvalidValue;
         if (A.lim == LIM_VANLEER) return col_fluid_launch<V, HSE, GRAV, LIM_VANLEER, FT1>(A, s);
         if (A.lim == LIM_MINMOD) return col_fluid_launch<V, HSE, GRAV, LIM_MINMOD, FT1>(A, s);
         return cudaErrorInvalidValue;
     } else {
+        // irregular mesh: widths along d (limiter read at run time)
+        if (A.wd) return col_fluid_launch<V, HSE, GRAV, -1, FT1, true>(A, s);
         return col_fluid_launch<V, HSE, GRAV, -1, FT1>(A, s);
     }
 }
@@ -68,26 +76,34 @@ cudaError_t col_fluid(const ColFluidArgs<typename VT<V>::S> &A, bool hse, bool f
     }
 }
 
-template <class V, int LIM, bool FT1>
+template <class V, int LIM, bool FT1, bool NU = false>
 static cudaError_t col_ct_launch(const ColCTArgs<typename VT<V>::S> &A, cudaStream_t s)
 {
     // one warp per 31 W columns of a row (plus a halo lane)
     const int segc = 31 * VT<V>::W;
     const long long warps = (long long)((A.nf + segc - 1) / segc) * A.no;
-    ct_col_kernel<V, LIM, FT1><<<col_grid(warps * 32, 128), 128, 0, s>>>(A);
+    ct_col_kernel<V, LIM, FT1, NU><<<col_grid(warps * 32, 128), 128, 0, s>>>(A);
     return cudaGetLastError();
 }
 
 template <class V> cudaError_t col_ct(const ColCTArgs<typename VT<V>::S> &A, bool ft1, cudaStream_t s)
 {
+    const bool nu = A.wd != nullptr;
+    if (nu && (!A.wf || !A.wo)) return cudaErrorInvalidValue;
     if constexpr (VT<V>::F64) {
+        if (nu) return ft1 ? col_ct_launch<V, -1, true, true>(A, s) : col_ct_launch<V, -1, false, true>(A, s);
         return ft1 ? col_ct_launch<V, -1, true>(A, s) : col_ct_launch<V, -1, false>(A, s);
+    } else if constexpr (std::is_same<V, P2>::value) {
+        if (nu) return cudaErrorInvalidValue;
+        if (A.lim == LIM_VANLEER) return col_ct_launch<V, LIM_VANLEER, true>(A, s);
+        if (A.lim == LIM_MINMOD) return col_ct_launch<V, LIM_MINMOD, true>(A, s);
+        return cudaErrorInvalidValue;
     } else {
+        if (nu) return col_ct_launch<V, -1, true, true>(A, s);
         // FP32: compile-time limiters for the throughput path
         if (A.lim == LIM_VANLEER) return col_ct_launch<V, LIM_VANLEER, true>(A, s);
         if (A.lim == LIM_MINMOD) return col_ct_launch<V, LIM_MINMOD, true>(A, s);
-        if constexpr (std::is_same<V, P2>::value) return cudaErrorInvalidValue;
-        else return col_ct_launch<V, -1, true>(A, s);
+        return col_ct_launch<V, -1, true>(A, s);
     }
 }
 

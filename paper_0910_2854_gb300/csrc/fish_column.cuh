@@ -49,6 +49,7 @@ template <class S> struct ColFluidArgs {
     // reciprocal (atomic minimum)
     unsigned long long *cfl_min;
     S rh[3];
+    const S *wd = nullptr;  // irregular mesh (kernels built with NU): the n cell widths along d
 };
 
 template <class S> struct ColCTArgs {
@@ -62,6 +63,8 @@ template <class S> struct ColCTArgs {
     int bc;
     int lim;
     double h, hf, ho;       // cell widths along d, the fast and the other axis
+    // irregular mesh (kernels built with NU): cell widths along d, fast, other
+    const S *wd = nullptr, *wf = nullptr, *wo = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -256,10 +259,21 @@ __device__ __forceinline__ void cflux1(const CCell<V> &a, const CCell<V> &b, V p
 // (eq0160-eq0230; one freezing speed per interface, reading C-2; HSE form of
 // the slope differences, reading C-19).  The hybrid limiter is taken only by
 // the one-column kernels with the limiter read at run time.
-template <class V, bool HSE, int LIM>
+// NU (irregular mesh, reading C-25): each one-sided difference is divided
+// by the distance of the centres it joins and the limited slope carried
+// over half the width of its own cell (w1 for F+, w2 for F-).
+template <class V, bool HSE, int LIM, bool NU = false>
 __device__ __forceinline__ void cflux2(const CCell<V> &c0, const CCell<V> &c1, const CCell<V> &c2, const CCell<V> &c3,
-                                       V ph0, V ph1, V ph2, V ph3, V F[5], int lim)
+                                       V ph0, V ph1, V ph2, V ph3, V F[5], int lim, V w0 = V(), V w1 = V(),
+                                       V w2 = V(), V w3 = V())
 {
+    V gl = w0, gc = w1, gr = w2;
+    if constexpr (NU) {
+        const V half = vb<V>(0.5f);
+        gl = half * (w0 + w1);
+        gc = half * (w1 + w2);
+        gr = half * (w2 + w3);
+    }
     if constexpr (LIM < 0 && VT<V>::W == 1) {
         // hybrid limiter (Sec. 2.2): minmod where either cell of the
         // interface moves faster than its sound speed, else Van Leer (reading C-21)
@@ -276,8 +290,14 @@ __device__ __forceinline__ void cflux2(const CCell<V> &c0, const CCell<V> &c1, c
             const V df0 = c1.F[i] - c0.F[i], du0 = c1.u[i] - c0.u[i];
             const V df1 = c2.F[i] - c1.F[i], du1 = c2.u[i] - c1.u[i];
             const V df2 = c3.F[i] - c2.F[i], du2 = c3.u[i] - c2.u[i];
-            const V slp = vlimit<LIM>(vfma(D, du0, df0), vfma(D, du1, df1), lim);
-            const V slm = vlimit<LIM>(vfma(nD, du1, df1), vfma(nD, du2, df2), lim);
+            V slp, slm;
+            if constexpr (NU) {
+                slp = w1 * vlimit<LIM>(vdiv(vfma(D, du0, df0), gl), vdiv(vfma(D, du1, df1), gc), lim);
+                slm = w2 * vlimit<LIM>(vdiv(vfma(nD, du1, df1), gc), vdiv(vfma(nD, du2, df2), gr), lim);
+            } else {
+                slp = vlimit<LIM>(vfma(D, du0, df0), vfma(D, du1, df1), lim);
+                slm = vlimit<LIM>(vfma(nD, du1, df1), vfma(nD, du2, df2), lim);
+            }
             F[i] = vfma(vb<V>(0.5f), vfma(nD, du1, c1.F[i] + c2.F[i]), vb<V>(0.25f) * (slp - slm));
         }
     } else if constexpr (!HSE) {
@@ -290,8 +310,14 @@ __device__ __forceinline__ void cflux2(const CCell<V> &c0, const CCell<V> &c1, c
             const V fm1 = 0.5 * (c1.F[i] - D * c1.u[i]);
             const V fm2 = 0.5 * (c2.F[i] - D * c2.u[i]);
             const V fm3 = 0.5 * (c3.F[i] - D * c3.u[i]);
-            const V slp = vlimit<LIM>(fp1 - fp0, fp2 - fp1, lim);
-            const V slm = vlimit<LIM>(fm2 - fm1, fm3 - fm2, lim);
+            V slp, slm;
+            if constexpr (NU) {
+                slp = w1 * vlimit<LIM>((fp1 - fp0) / gl, (fp2 - fp1) / gc, lim);
+                slm = w2 * vlimit<LIM>((fm2 - fm1) / gc, (fm3 - fm2) / gr, lim);
+            } else {
+                slp = vlimit<LIM>(fp1 - fp0, fp2 - fp1, lim);
+                slm = vlimit<LIM>(fm2 - fm1, fm3 - fm2, lim);
+            }
             F[i] = fp1 + fm2 + 0.5 * (slp - slm);
         }
     } else {
@@ -311,8 +337,14 @@ __device__ __forceinline__ void cflux2(const CCell<V> &c0, const CCell<V> &c1, c
             const V fp_r = half * ((c2.F[i] - c1.F[i]) + q1);
             const V fm_l = half * ((c2.F[i] - c1.F[i]) - q1);
             const V fm_r = half * ((c3.F[i] - c2.F[i]) - q2);
-            const V slp = vlimit<LIM>(fp_l, fp_r, lim);
-            const V slm = vlimit<LIM>(fm_l, fm_r, lim);
+            V slp, slm;
+            if constexpr (NU) {
+                slp = w1 * vlimit<LIM>(vdiv(fp_l, gl), vdiv(fp_r, gc), lim);
+                slm = w2 * vlimit<LIM>(vdiv(fm_l, gc), vdiv(fm_r, gr), lim);
+            } else {
+                slp = vlimit<LIM>(fp_l, fp_r, lim);
+                slm = vlimit<LIM>(fm_l, fm_r, lim);
+            }
             F[i] = half * (c1.F[i] + c2.F[i]) - half * q1 + half * (slp - slm);
         }
     }
@@ -354,6 +386,7 @@ template <class V> struct FRaw {
     V bo, bom; // other-axis transverse face field at own / lower face
     V phi;
     typename VT<V>::S bfm;  // fast-axis field at the face below the first column
+    V w;       // cell width along d (irregular mesh)
 };
 
 template <class V> struct FMarch {
@@ -368,6 +401,7 @@ template <class V> struct FMarch {
     V phm2;              // potential of raw cell r-2
     Checks<V> chk;
     V cflr;              // largest CFL rate of the output cells (CFLF)
+    V w0, w1, w2, w3, w4;  // irregular mesh: widths of raw cells r, r-1, .. r-4
 };
 
 template <class S> struct FCtx {
@@ -402,6 +436,9 @@ __device__ __forceinline__ void fload_mapped(const ColFluidArgs<typename VT<V>::
         if constexpr (!VT<V>::F64)
             if (A.bc == BC_OUTFLOW && (s < 0 || s >= A.n)) R.phi = vb<V>(0.0f);
     }
+    // a ghost has the width of the cell it copies (reading C-23)
+    if constexpr (VT<V>::W == 1)
+        if (A.wd) R.w = A.wd[cc];
 }
 
 // load interior cell at element offset i (no map; its lower b_d face is the
@@ -450,8 +487,10 @@ enum : int { LD_NONE = 0, LD_DIRECT = 1, LD_MAPPED = 2, LD_DIRECT_PF = 3 };
 
 // One step of the march for raw cell r (K = r mod 4).  The raw data of cell
 // r is in M.R on entry (loaded by the previous step); the step loads raw
-// cell r+1 (kind LD) into M.R.  FT1: the fast axis is t1 (else t2).
-template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool CFLF, int K, int ST, int LD>
+// cell r+1 (kind LD) into M.R.  FT1: the fast axis is t1 (else t2).  NU:
+// irregular mesh along d (eq037): the cells' own widths replace h (the
+// widths of raw cells r .. r-4 ride along in M.w0 .. M.w4).
+template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool CFLF, bool NU, int K, int ST, int LD>
 __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S> &X,
                                       FMarch<V> &M, int r, V lam, V lamh, V hdt, V dt, V rtwoh)
 {
@@ -474,9 +513,17 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
         bbr[2] = bfc;
     }
     const V phr = GRAV ? M.R.phi : vb<V>(0.0f);  // no potential: phi = 0
+    if constexpr (NU) {
+        M.w4 = M.w3;
+        M.w3 = M.w2;
+        M.w2 = M.w1;
+        M.w1 = M.w0;
+        M.w0 = M.R.w;
+    }
     // prefetch raw cell r+1
     if constexpr (LD == LD_DIRECT || LD == LD_DIRECT_PF) {
         fload_direct<V, GRAV, FT1>(A, X, X.base + (long long)(r + 1) * A.sd, M.R);
+        if constexpr (NU) M.R.w = A.wd[r + 1];
         M.R.bdm = bd_r;
         if constexpr (LD == LD_DIRECT_PF) {
             const int pf = min(r + 1 + FISH_PF_DIST, A.n - 1);
@@ -505,16 +552,29 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
         // predicted half step of cell r-1 (eq0253; source eq0254, reading C-6)
         const CCell<V> &cp = M.C[p2];
         V up[5];
+        V lh = lamh;
+        if constexpr (NU) {
+            if constexpr (VT<V>::F64) lh = dt / (2.0 * M.w1);
+            else lh = vdiv(hdt, M.w1);
+        }
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
-            if constexpr (VT<V>::F64) up[k] = cp.u[k] - lamh * (M.F1[k2][k] - M.F1[p2][k]);
-            else up[k] = vfma(-lamh, M.F1[k2][k] - M.F1[p2][k], cp.u[k]);
+            if constexpr (VT<V>::F64) up[k] = cp.u[k] - lh * (M.F1[k2][k] - M.F1[p2][k]);
+            else up[k] = vfma(-lh, M.F1[k2][k] - M.F1[p2][k], cp.u[k]);
         }
         if (GRAV) {
-            // centred difference phi_r - phi_{r-2} (eq02513)
+            // centred difference phi_r - phi_{r-2} (eq02513; NU: over the
+            // centre span, reading C-26)
             V dphi;
-            if constexpr (VT<V>::F64) dphi = (phr - M.phm2) / (2.0 * A.h);
-            else dphi = (M.ph[p2] + M.phm2) * rtwoh;
+            if constexpr (NU) {
+                const V span = vb<V>(0.5f) * M.w2 + M.w1 + vb<V>(0.5f) * M.w0;
+                if constexpr (VT<V>::F64) dphi = (phr - M.phm2) / span;
+                else dphi = vdiv(M.ph[p2] + M.phm2, span);
+            } else if constexpr (VT<V>::F64) {
+                dphi = (phr - M.phm2) / (2.0 * A.h);
+            } else {
+                dphi = (M.ph[p2] + M.phm2) * rtwoh;
+            }
             up[1] = up[1] - hdt * cp.u[0] * dphi;
             up[4] = up[4] - hdt * cp.u[1] * dphi;
         }
@@ -524,19 +584,31 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
         if constexpr ((ST & ST_F2) != 0) {
             // corrector flux at (r-3, r-2) from predicted cells r-4 .. r-1 (eq0230)
             constexpr int s0 = K & 3, s1 = (K + 1) & 3, s2 = (K + 2) & 3;
-            cflux2<V, HSE, LIM>(M.P[s0], M.P[s1], M.P[s2], M.P[s3], M.q[s0], M.q[s1], M.q[s2], M.q[s3], M.F2[k2],
-                                A.lim);
+            cflux2<V, HSE, LIM, NU>(M.P[s0], M.P[s1], M.P[s2], M.P[s3], M.q[s0], M.q[s1], M.q[s2], M.q[s3],
+                                    M.F2[k2], A.lim, M.w4, M.w3, M.w2, M.w1);
             if constexpr ((ST & ST_OUT) != 0) {
+                V lo = lam;
+                if constexpr (NU) {
+                    if constexpr (VT<V>::F64) lo = dt / M.w3;
+                    else lo = vdiv(dt, M.w3);
+                }
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
-                    if constexpr (VT<V>::F64) un[k] = un[k] - lam * (M.F2[k2][k] - M.F2[p2][k]);
-                    else un[k] = vfma(-lam, M.F2[k2][k] - M.F2[p2][k], un[k]);
+                    if constexpr (VT<V>::F64) un[k] = un[k] - lo * (M.F2[k2][k] - M.F2[p2][k]);
+                    else un[k] = vfma(-lo, M.F2[k2][k] - M.F2[p2][k], un[k]);
                 }
                 if (GRAV) {
                     // corrector source from the predicted state (eq0255)
                     V dphi;
-                    if constexpr (VT<V>::F64) dphi = (M.q[s2] - M.q[s0]) / (2.0 * A.h);
-                    else dphi = (M.q[s0] + M.q[s1]) * rtwoh;
+                    if constexpr (NU) {
+                        const V span = vb<V>(0.5f) * M.w4 + M.w3 + vb<V>(0.5f) * M.w2;
+                        if constexpr (VT<V>::F64) dphi = (M.q[s2] - M.q[s0]) / span;
+                        else dphi = vdiv(M.q[s0] + M.q[s1], span);
+                    } else if constexpr (VT<V>::F64) {
+                        dphi = (M.q[s2] - M.q[s0]) / (2.0 * A.h);
+                    } else {
+                        dphi = (M.q[s0] + M.q[s1]) * rtwoh;
+                    }
                     un[1] = un[1] - dt * M.P[s1].u[0] * dphi;
                     un[4] = un[4] - dt * M.P[s1].u[1] * dphi;
                 }
@@ -572,16 +644,16 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
 
 // L_d over all columns.  The prologue runs raw cells -3 .. 2 (K = 1, 2, 3,
 // 0, 1, 2); boxes with n < 8 load everything through the map.
-template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool CFLF, int PLD>
+template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool CFLF, bool NU, int PLD>
 __device__ __forceinline__ void fprologue(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S> &X,
                                           FMarch<V> &M, V lam, V lamh, V hdt, V dt, V rtwoh)
 {
-    fstep<V, HSE, GRAV, LIM, FT1, CFLF, 1, 0, LD_MAPPED>(A, X, M, -3, lam, lamh, hdt, dt, rtwoh);
-    fstep<V, HSE, GRAV, LIM, FT1, CFLF, 2, ST_F1, LD_MAPPED>(A, X, M, -2, lam, lamh, hdt, dt, rtwoh);
-    fstep<V, HSE, GRAV, LIM, FT1, CFLF, 3, ST_F1 | ST_PRED, PLD>(A, X, M, -1, lam, lamh, hdt, dt, rtwoh);
-    fstep<V, HSE, GRAV, LIM, FT1, CFLF, 0, ST_F1 | ST_PRED, PLD>(A, X, M, 0, lam, lamh, hdt, dt, rtwoh);
-    fstep<V, HSE, GRAV, LIM, FT1, CFLF, 1, ST_F1 | ST_PRED, PLD>(A, X, M, 1, lam, lamh, hdt, dt, rtwoh);
-    fstep<V, HSE, GRAV, LIM, FT1, CFLF, 2, ST_F1 | ST_PRED | ST_F2, PLD>(A, X, M, 2, lam, lamh, hdt, dt, rtwoh);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, 0, LD_MAPPED>(A, X, M, -3, lam, lamh, hdt, dt, rtwoh);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ST_F1, LD_MAPPED>(A, X, M, -2, lam, lamh, hdt, dt, rtwoh);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ST_F1 | ST_PRED, PLD>(A, X, M, -1, lam, lamh, hdt, dt, rtwoh);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ST_F1 | ST_PRED, PLD>(A, X, M, 0, lam, lamh, hdt, dt, rtwoh);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ST_F1 | ST_PRED, PLD>(A, X, M, 1, lam, lamh, hdt, dt, rtwoh);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ST_F1 | ST_PRED | ST_F2, PLD>(A, X, M, 2, lam, lamh, hdt, dt, rtwoh);
 }
 
 #ifndef FISH_COL_MINB
@@ -592,7 +664,7 @@ __device__ __forceinline__ void fprologue(const ColFluidArgs<typename VT<V>::S> 
 #endif
 
 // The march of thread cid (column group cid of the box described by A).
-template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool CFLF>
+template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool CFLF, bool NU = false>
 __device__ __forceinline__ void fluid_columns(const ColFluidArgs<typename VT<V>::S> &A, long long cid)
 {
     using S = typename VT<V>::S;
@@ -618,31 +690,32 @@ __device__ __forceinline__ void fluid_columns(const ColFluidArgs<typename VT<V>:
     M.cflr = vb<V>(0.0f);
     M.phm2 = vb<V>(0.0f);
     M.ph[0] = M.ph[1] = vb<V>(0.0f);
+    M.w0 = M.w1 = M.w2 = M.w3 = M.w4 = vb<V>(1.0f);
     fload_mapped<V, GRAV, FT1>(A, X, -3, M.R);
     constexpr int ALL = ST_F1 | ST_PRED | ST_F2 | ST_OUT;
     int r = 3;
     if (n >= 8) {
-        fprologue<V, HSE, GRAV, LIM, FT1, CFLF, LD_DIRECT>(A, X, M, lam, lamh, hdt, dt, rtwoh);
+        fprologue<V, HSE, GRAV, LIM, FT1, CFLF, NU, LD_DIRECT>(A, X, M, lam, lamh, hdt, dt, rtwoh);
         // steady state: the four steps r .. r+3 prefetch interior cells
 #pragma unroll 1
         for (; r + 4 <= n - 1; r += 4) {
-            fstep<V, HSE, GRAV, LIM, FT1, CFLF, 3, ALL, LD_DIRECT_PF>(A, X, M, r, lam, lamh, hdt, dt, rtwoh);
-            fstep<V, HSE, GRAV, LIM, FT1, CFLF, 0, ALL, LD_DIRECT_PF>(A, X, M, r + 1, lam, lamh, hdt, dt, rtwoh);
-            fstep<V, HSE, GRAV, LIM, FT1, CFLF, 1, ALL, LD_DIRECT_PF>(A, X, M, r + 2, lam, lamh, hdt, dt, rtwoh);
-            fstep<V, HSE, GRAV, LIM, FT1, CFLF, 2, ALL, LD_DIRECT_PF>(A, X, M, r + 3, lam, lamh, hdt, dt, rtwoh);
+            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ALL, LD_DIRECT_PF>(A, X, M, r, lam, lamh, hdt, dt, rtwoh);
+            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ALL, LD_DIRECT_PF>(A, X, M, r + 1, lam, lamh, hdt, dt, rtwoh);
+            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ALL, LD_DIRECT_PF>(A, X, M, r + 2, lam, lamh, hdt, dt, rtwoh);
+            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ALL, LD_DIRECT_PF>(A, X, M, r + 3, lam, lamh, hdt, dt, rtwoh);
         }
     } else {
-        fprologue<V, HSE, GRAV, LIM, FT1, CFLF, LD_MAPPED>(A, X, M, lam, lamh, hdt, dt, rtwoh);
+        fprologue<V, HSE, GRAV, LIM, FT1, CFLF, NU, LD_MAPPED>(A, X, M, lam, lamh, hdt, dt, rtwoh);
     }
     // tail: raw cells r .. n+2 (r = 3 mod 4, at most seven), loads through
     // the map (harmless beyond n+2)
-    if (r <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, 3, ALL, LD_MAPPED>(A, X, M, r, lam, lamh, hdt, dt, rtwoh);
-    if (r + 1 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, 0, ALL, LD_MAPPED>(A, X, M, r + 1, lam, lamh, hdt, dt, rtwoh);
-    if (r + 2 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, 1, ALL, LD_MAPPED>(A, X, M, r + 2, lam, lamh, hdt, dt, rtwoh);
-    if (r + 3 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, 2, ALL, LD_MAPPED>(A, X, M, r + 3, lam, lamh, hdt, dt, rtwoh);
-    if (r + 4 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, 3, ALL, LD_MAPPED>(A, X, M, r + 4, lam, lamh, hdt, dt, rtwoh);
-    if (r + 5 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, 0, ALL, LD_MAPPED>(A, X, M, r + 5, lam, lamh, hdt, dt, rtwoh);
-    if (r + 6 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, 1, ALL, LD_NONE>(A, X, M, r + 6, lam, lamh, hdt, dt, rtwoh);
+    if (r <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ALL, LD_MAPPED>(A, X, M, r, lam, lamh, hdt, dt, rtwoh);
+    if (r + 1 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ALL, LD_MAPPED>(A, X, M, r + 1, lam, lamh, hdt, dt, rtwoh);
+    if (r + 2 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ALL, LD_MAPPED>(A, X, M, r + 2, lam, lamh, hdt, dt, rtwoh);
+    if (r + 3 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ALL, LD_MAPPED>(A, X, M, r + 3, lam, lamh, hdt, dt, rtwoh);
+    if (r + 4 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ALL, LD_MAPPED>(A, X, M, r + 4, lam, lamh, hdt, dt, rtwoh);
+    if (r + 5 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ALL, LD_MAPPED>(A, X, M, r + 5, lam, lamh, hdt, dt, rtwoh);
+    if (r + 6 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ALL, LD_NONE>(A, X, M, r + 6, lam, lamh, hdt, dt, rtwoh);
     const unsigned fl = checks_flags(M.chk);
     if (fl) atomicOr(A.flags, fl);
     if constexpr (CFLF) {
@@ -664,11 +737,11 @@ __device__ __forceinline__ void fluid_columns(const ColFluidArgs<typename VT<V>:
     }
 }
 
-template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool CFLF = false>
+template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool CFLF = false, bool NU = false>
 __global__ void __launch_bounds__(128, VT<V>::F64 ? 1 : (VT<V>::W == 2 || HSE ? FISH_COL_MINB : FISH_COL_MINB1))
     fluid_col_kernel(const ColFluidArgs<typename VT<V>::S> A)
 {
-    fluid_columns<V, HSE, GRAV, LIM, FT1, CFLF>(A, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    fluid_columns<V, HSE, GRAV, LIM, FT1, CFLF, NU>(A, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -685,11 +758,27 @@ template <class V> struct CFace {
     V f[2];    // corrector flux at interface (s-4)'
 };
 
+// Widths along d of cells s, s-1 .. s-5 (irregular mesh).
+template <class V> struct CWid {
+    V w0, w1, w2, w3, w4, w5;
+};
+
+// Edge velocity between cells a and b of a face pencil (eq0364): the mean,
+// or with NU the linear interpolation to the interface (reading C-27).
+template <class V, bool NU> __device__ __forceinline__ V cedge(V va, V vb_, V wa, V wb)
+{
+    if constexpr (!NU) return vb<V>(0.5f) * (va + vb_);
+    else if constexpr (VT<V>::F64) return (wb * va + wa * vb_) / (wa + wb);
+    else return vdiv(vfma(wb, va, wa * vb_), wa + wb);
+}
+
 // Advance a face pencil by cell s (K = s mod 4) with face velocity vt and
 // field bf.  With OUT, bnew receives the updated face field of cell s-4 and
-// f[K & 1] holds the corrector flux at (s-4)'.
-template <class V, int LIM, int K, bool PRE1, bool PRE2, bool CORR, bool OUT>
-__device__ __forceinline__ void cface(CFace<V> &P, V vt, V bf, V lamh, V lam, V &bnew, int lim)
+// f[K & 1] holds the corrector flux at (s-4)'.  NU: irregular mesh along d
+// (widths in cw, eq037 and reading C-25/C-27; dt for the per-cell factors).
+template <class V, int LIM, int K, bool PRE1, bool PRE2, bool CORR, bool OUT, bool NU = false>
+__device__ __forceinline__ void cface(CFace<V> &P, V vt, V bf, V lamh, V lam, V &bnew, int lim,
+                                      const CWid<V> &cw = CWid<V>(), V dt = V())
 {
     constexpr int k1 = (K + 3) & 3, k2 = (K + 2) & 3, kp = (K + 1) & 3;
     constexpr int e = K & 1, o = (K + 1) & 1;
@@ -702,22 +791,43 @@ __device__ __forceinline__ void cface(CFace<V> &P, V vt, V bf, V lamh, V lam, V 
     if constexpr (PRE1) {
         // first-order upwind flux at (s-2)' (eq0363, edge velocity eq0364;
         // tie v = 0 takes the right cell, reading C-7)
-        const V vbar = vb<V>(0.5f) * (P.vh[k2] + vh);
+        const V vbar = cedge<V, NU>(P.vh[k2], vh, cw.w2, cw.w1);
         P.f1[e] = vsel_pos(vbar, P.w[e], P.w[o]);
     }
     if constexpr (PRE2) {
         // predictor half step of the face field at s-2
         V bp;
-        if constexpr (VT<V>::F64) bp = P.bf[k2] - lamh * (P.f1[e] - P.f1[o]);
-        else bp = vfma(-lamh, P.f1[e] - P.f1[o], P.bf[k2]);
+        V lh = lamh;
+        if constexpr (NU) {
+            if constexpr (VT<V>::F64) lh = dt / (2.0 * cw.w2);
+            else lh = vdiv(vb<V>(0.5f) * dt, cw.w2);
+        }
+        if constexpr (VT<V>::F64) bp = P.bf[k2] - lh * (P.f1[e] - P.f1[o]);
+        else bp = vfma(-lh, P.f1[e] - P.f1[o], P.bf[k2]);
         P.wp[k2] = P.vh[k2] * bp;
     }
     if constexpr (CORR) {
         // corrector flux at q' = (s-4)': piecewise-linear TVD about the
         // upwind cell (reading C-10)
-        const V vbar = vb<V>(0.5f) * (P.vh[K] + P.vh[kp]);
+        const V vbar = cedge<V, NU>(P.vh[K], P.vh[kp], cw.w4, cw.w3);
         const V wm = P.wp[k1], w0 = P.wp[K], w1 = P.wp[kp], w2 = P.wp[k2];
-        if constexpr (VT<V>::F64) {
+        if constexpr (NU) {
+            // slopes per unit length over the centre distances, carried over
+            // half the upwind cell (reading C-25)
+            const V half = vb<V>(0.5f);
+            const V gl = half * (cw.w5 + cw.w4), gc = half * (cw.w4 + cw.w3), gr = half * (cw.w3 + cw.w2);
+            if constexpr (VT<V>::F64) {
+                P.f[e] = vbar > 0.0 ? w0 + 0.5 * cw.w4 * vlimit<LIM>((w0 - wm) / gl, (w1 - w0) / gc, lim)
+                                    : w1 - 0.5 * cw.w3 * vlimit<LIM>((w1 - w0) / gc, (w2 - w1) / gr, lim);
+            } else {
+                const V d0 = vdiv(w0 - wm, gl), d1 = vdiv(w1 - w0, gc), d2 = vdiv(w2 - w1, gr);
+                const V la = vsel_pos(vbar, d0, d1);
+                const V lb = vsel_pos(vbar, d1, d2);
+                const V base = vsel_pos(vbar, w0, w1);
+                const V sg = vsel_pos(vbar, half * cw.w4, -half * cw.w3);
+                P.f[e] = vfma(sg, vlimit<LIM>(la, lb, lim), base);
+            }
+        } else if constexpr (VT<V>::F64) {
             P.f[e] = vbar > 0.0 ? w0 + 0.5 * vlimit<LIM>(w0 - wm, w1 - w0, lim) : w1 - 0.5 * vlimit<LIM>(w1 - w0, w2 - w1, lim);
         } else {
             // select the upwind operands, then limit once
@@ -729,8 +839,13 @@ __device__ __forceinline__ void cface(CFace<V> &P, V vt, V bf, V lamh, V lam, V 
             P.f[e] = vfma(sg, vlimit<LIM>(la, lb, lim), base);
         }
         if constexpr (OUT) {
-            if constexpr (VT<V>::F64) bnew = P.bf[K] - lam * (P.f[e] - P.f[o]);
-            else bnew = vfma(-lam, P.f[e] - P.f[o], P.bf[K]);
+            V lo = lam;
+            if constexpr (NU) {
+                if constexpr (VT<V>::F64) lo = dt / cw.w4;
+                else lo = vdiv(dt, cw.w4);
+            }
+            if constexpr (VT<V>::F64) bnew = P.bf[K] - lo * (P.f[e] - P.f[o]);
+            else bnew = vfma(-lo, P.f[e] - P.f[o], P.bf[K]);
         }
     }
     P.bf[K] = bf;
@@ -752,6 +867,8 @@ template <class S> struct CTCtx {
     long long oom, oop;  // offsets to the other-axis rows below / above (mapped)
     bool active;         // lane stores its columns
     bool fixy;           // halo lane at an outflow edge: its upper column is a copy of the lower
+    S wfa, wfb;          // irregular mesh: widths of the lane's column and the one above (fast axis)
+    S woa, wop, wom;     // widths of the lane's row and the rows above / below (other axis)
 };
 
 template <class V> struct CTRaw {
@@ -759,6 +876,7 @@ template <class V> struct CTRaw {
     typename VT<V>::S rf, mf;   // rho, m_d of the column above the lane's last column
     V bF, bO, bOm;              // fast-axis faces; other-axis faces of this and the previous row
     V bdo;                      // b_d of the output cell s-4
+    V w;                        // width along d of cell s (irregular mesh)
 };
 
 template <class V> __device__ __forceinline__ void fixy_(V &a, bool f)
@@ -770,11 +888,13 @@ template <class V> __device__ __forceinline__ void fixy_(V &a, bool f)
 
 // load the raw inputs of cell s (MAPPED: s through the boundary map; OUTLD:
 // also b_d of the output cell s-4, which is interior)
-template <class V, bool MAPPED, bool OUTLD>
+template <class V, bool MAPPED, bool OUTLD, bool NU>
 __device__ __forceinline__ void ctload(const ColCTArgs<typename VT<V>::S> &A, const CTCtx<typename VT<V>::S> &X, int s,
                                        CTRaw<V> &R)
 {
-    const long long i = X.base + (long long)(MAPPED ? gmap(s, A.n, A.bc) : s) * A.sd;
+    const int sm = MAPPED ? gmap(s, A.n, A.bc) : s;
+    const long long i = X.base + (long long)sm * A.sd;
+    if constexpr (NU) R.w = A.wd[sm];  // a ghost has the width of its image (reading C-23)
     R.rc = vload<V>(A.rho, i);
     R.mc = vload<V>(A.md, i);
     R.ro = vload<V>(A.rho, i + X.oop);
@@ -816,6 +936,7 @@ __device__ __forceinline__ void ctprefetch(const ColCTArgs<typename VT<V>::S> &A
 template <class V> struct CTMarch {
     CFace<V> PF, PO, POm;   // fast-axis faces above, other-axis faces above / below
     CTRaw<V> R;             // raw inputs of the next cell
+    CWid<V> cw;             // irregular mesh: widths along d of cells s-1 .. s-5
 };
 
 template <class V> __device__ __forceinline__ V shfl_up1(V a)
@@ -831,10 +952,20 @@ enum : int { CL_NONE = 0, CL_DIRECT = 1, CL_DIRECT_PF = 2, CL_MAPPED = 3 };
 
 // One cell s of the CT march (K = s mod 4); the raw inputs of s are in M.R.
 // Next loads cell s+1 (kind LD; NOUT: with b_d of cell s-3 for its output).
-template <class V, int LIM, bool FT1, int K, bool PRE1, bool PRE2, bool CORR, bool OUT, int LD, bool NOUT>
+template <class V, int LIM, bool FT1, bool NU, int K, bool PRE1, bool PRE2, bool CORR, bool OUT, int LD, bool NOUT>
 __device__ __forceinline__ void ctstep(const ColCTArgs<typename VT<V>::S> &A, const CTCtx<typename VT<V>::S> &X,
-                                       CTMarch<V> &M, int s, V lamh, V lam, V lamf, V lamo)
+                                       CTMarch<V> &M, int s, V lamh, V lam, V lamf, V lamo, V dt)
 {
+    // widths of cells s .. s-5 for this step (the width of cell s arrived
+    // with its raw inputs)
+    if constexpr (NU) {
+        M.cw.w5 = M.cw.w4;
+        M.cw.w4 = M.cw.w3;
+        M.cw.w3 = M.cw.w2;
+        M.cw.w2 = M.cw.w1;
+        M.cw.w1 = M.cw.w0;
+        M.cw.w0 = M.R.w;
+    }
     // consume the raw inputs of cell s
     const V vc = vdiv(M.R.mc, M.R.rc);
     const V vop = vdiv(M.R.mo, M.R.ro);
@@ -846,17 +977,33 @@ __device__ __forceinline__ void ctstep(const ColCTArgs<typename VT<V>::S> &A, co
     const V bdo = M.R.bdo;
     // load cell s+1
     if constexpr (LD == CL_DIRECT || LD == CL_DIRECT_PF) {
-        ctload<V, false, NOUT>(A, X, s + 1, M.R);
+        ctload<V, false, NOUT, NU>(A, X, s + 1, M.R);
         if constexpr (LD == CL_DIRECT_PF)
             ctprefetch<V>(A, X, X.base + (long long)min(s + 1 + FISH_PF_DIST, A.n - 1) * A.sd);
     } else if constexpr (LD == CL_MAPPED) {
-        ctload<V, true, NOUT>(A, X, s + 1, M.R);
+        ctload<V, true, NOUT, NU>(A, X, s + 1, M.R);
     }
     const V half = vb<V>(0.5f);
+    // face velocities (eq0361): the mean of the two cells across the face,
+    // or on an irregular mesh their linear interpolation to it (reading C-27)
+    V vtF, vtO, vtOm;
+    if constexpr (!NU) {
+        vtF = half * (vc + vfp);
+        vtO = half * (vc + vop);
+        vtOm = half * (vom + vc);
+    } else if constexpr (VT<V>::F64) {
+        vtF = (X.wfb * vc + X.wfa * vfp) / (X.wfa + X.wfb);
+        vtO = (X.wop * vc + X.woa * vop) / (X.woa + X.wop);
+        vtOm = (X.woa * vom + X.wom * vc) / (X.wom + X.woa);
+    } else {
+        vtF = vdiv(vfma(V(X.wfb), vc, V(X.wfa) * vfp), V(X.wfa + X.wfb));
+        vtO = vdiv(vfma(V(X.wop), vc, V(X.woa) * vop), V(X.woa + X.wop));
+        vtOm = vdiv(vfma(V(X.woa), vom, V(X.wom) * vc), V(X.wom + X.woa));
+    }
     V nF, nO, dummy;
-    cface<V, LIM, K, PRE1, PRE2, CORR, OUT>(M.PF, half * (vc + vfp), bF, lamh, lam, nF, A.lim);
-    cface<V, LIM, K, PRE1, PRE2, CORR, OUT>(M.PO, half * (vc + vop), bO, lamh, lam, nO, A.lim);
-    cface<V, LIM, K, PRE1, PRE2, CORR, false>(M.POm, half * (vom + vc), bOm, lamh, lam, dummy, A.lim);
+    cface<V, LIM, K, PRE1, PRE2, CORR, OUT, NU>(M.PF, vtF, bF, lamh, lam, nF, A.lim, M.cw, dt);
+    cface<V, LIM, K, PRE1, PRE2, CORR, OUT, NU>(M.PO, vtO, bO, lamh, lam, nO, A.lim, M.cw, dt);
+    cface<V, LIM, K, PRE1, PRE2, CORR, false, NU>(M.POm, vtOm, bOm, lamh, lam, dummy, A.lim, M.cw, dt);
     if constexpr (OUT) {
         constexpr int e = K & 1;
         // edge flux of the fast-axis face below: the upper pencil of the lane beneath
@@ -891,7 +1038,7 @@ __device__ __forceinline__ void ctstep(const ColCTArgs<typename VT<V>::S> &A, co
 // a warp takes the same steps (shuffles); lanes without columns of their
 // own repeat a valid column and store nothing.
 // The march of warp gw (31 W columns of one row) of the box described by A.
-template <class V, int LIM, bool FT1>
+template <class V, int LIM, bool FT1, bool NU = false>
 __device__ __forceinline__ void ct_columns(const ColCTArgs<typename VT<V>::S> &A, long long gw, int lane)
 {
     using S = typename VT<V>::S;
@@ -920,10 +1067,23 @@ __device__ __forceinline__ void ct_columns(const ColCTArgs<typename VT<V>::S> &A
     X.oom = (long long)(gmap(ob - 1, A.no, A.bc) - ob) * A.so;
     X.oop = (long long)(gmap(ob + 1, A.no, A.bc) - ob) * A.so;
     const double dtd = *A.dt;
+    const V dtv = vb<V>(S(dtd));
     const V lamh = vb<V>(S(dtd / (2.0 * A.h)));
     const V lam = vb<V>(S(dtd / A.h));
-    const V lamf = vb<V>(S(dtd / A.hf));
-    const V lamo = vb<V>(S(dtd / A.ho));
+    V lamf = vb<V>(S(dtd / A.hf));
+    V lamo = vb<V>(S(dtd / A.ho));
+    if constexpr (NU) {
+        // irregular mesh: widths of the lane's column and its neighbours (a
+        // halo or ghost column has the width of its image), and the
+        // constraint factors of b_d over the cell's own transverse widths
+        X.wfa = A.wf[cb];
+        X.wfb = A.wf[cfp];
+        X.woa = A.wo[ob];
+        X.wop = A.wo[gmap(ob + 1, A.no, A.bc)];
+        X.wom = A.wo[gmap(ob - 1, A.no, A.bc)];
+        lamf = vb<V>(S(dtd / (double)X.wfa));
+        lamo = vb<V>(S(dtd / (double)X.woa));
+    }
     const int n = A.n;
     CTMarch<V> M;
     {
@@ -934,50 +1094,51 @@ __device__ __forceinline__ void ct_columns(const ColCTArgs<typename VT<V>::S> &A
         M.PF = M.PO = M.POm = z;
     }
     M.R.bdo = vb<V>(0.0f);
-    ctload<V, true, false>(A, X, -4, M.R);
+    M.cw.w0 = M.cw.w1 = M.cw.w2 = M.cw.w3 = M.cw.w4 = M.cw.w5 = vb<V>(1.0f);
+    ctload<V, true, false, NU>(A, X, -4, M.R);
     // prologue s = -4 .. 3 (stages switch on at -1, 0, 3); cells 0 .. 3 are
     // loaded directly when n >= 4
-    ctstep<V, LIM, FT1, 0, false, false, false, false, CL_MAPPED, false>(A, X, M, -4, lamh, lam, lamf, lamo);
-    ctstep<V, LIM, FT1, 1, false, false, false, false, CL_MAPPED, false>(A, X, M, -3, lamh, lam, lamf, lamo);
-    ctstep<V, LIM, FT1, 2, false, false, false, false, CL_MAPPED, false>(A, X, M, -2, lamh, lam, lamf, lamo);
+    ctstep<V, LIM, FT1, NU, 0, false, false, false, false, CL_MAPPED, false>(A, X, M, -4, lamh, lam, lamf, lamo, dtv);
+    ctstep<V, LIM, FT1, NU, 1, false, false, false, false, CL_MAPPED, false>(A, X, M, -3, lamh, lam, lamf, lamo, dtv);
+    ctstep<V, LIM, FT1, NU, 2, false, false, false, false, CL_MAPPED, false>(A, X, M, -2, lamh, lam, lamf, lamo, dtv);
     int s = 4;
     if (n >= 8) {
-        ctstep<V, LIM, FT1, 3, true, false, false, false, CL_DIRECT, false>(A, X, M, -1, lamh, lam, lamf, lamo);
-        ctstep<V, LIM, FT1, 0, true, true, false, false, CL_DIRECT, false>(A, X, M, 0, lamh, lam, lamf, lamo);
-        ctstep<V, LIM, FT1, 1, true, true, false, false, CL_DIRECT, false>(A, X, M, 1, lamh, lam, lamf, lamo);
-        ctstep<V, LIM, FT1, 2, true, true, false, false, CL_DIRECT, false>(A, X, M, 2, lamh, lam, lamf, lamo);
-        ctstep<V, LIM, FT1, 3, true, true, true, false, CL_DIRECT, true>(A, X, M, 3, lamh, lam, lamf, lamo);
+        ctstep<V, LIM, FT1, NU, 3, true, false, false, false, CL_DIRECT, false>(A, X, M, -1, lamh, lam, lamf, lamo, dtv);
+        ctstep<V, LIM, FT1, NU, 0, true, true, false, false, CL_DIRECT, false>(A, X, M, 0, lamh, lam, lamf, lamo, dtv);
+        ctstep<V, LIM, FT1, NU, 1, true, true, false, false, CL_DIRECT, false>(A, X, M, 1, lamh, lam, lamf, lamo, dtv);
+        ctstep<V, LIM, FT1, NU, 2, true, true, false, false, CL_DIRECT, false>(A, X, M, 2, lamh, lam, lamf, lamo, dtv);
+        ctstep<V, LIM, FT1, NU, 3, true, true, true, false, CL_DIRECT, true>(A, X, M, 3, lamh, lam, lamf, lamo, dtv);
         // steady state: the four steps s .. s+3 load interior cells s+1 .. s+4
 #pragma unroll 1
         for (; s + 4 <= n - 1; s += 4) {
-            ctstep<V, LIM, FT1, 0, true, true, true, true, CL_DIRECT_PF, true>(A, X, M, s, lamh, lam, lamf, lamo);
-            ctstep<V, LIM, FT1, 1, true, true, true, true, CL_DIRECT_PF, true>(A, X, M, s + 1, lamh, lam, lamf, lamo);
-            ctstep<V, LIM, FT1, 2, true, true, true, true, CL_DIRECT_PF, true>(A, X, M, s + 2, lamh, lam, lamf, lamo);
-            ctstep<V, LIM, FT1, 3, true, true, true, true, CL_DIRECT_PF, true>(A, X, M, s + 3, lamh, lam, lamf, lamo);
+            ctstep<V, LIM, FT1, NU, 0, true, true, true, true, CL_DIRECT_PF, true>(A, X, M, s, lamh, lam, lamf, lamo, dtv);
+            ctstep<V, LIM, FT1, NU, 1, true, true, true, true, CL_DIRECT_PF, true>(A, X, M, s + 1, lamh, lam, lamf, lamo, dtv);
+            ctstep<V, LIM, FT1, NU, 2, true, true, true, true, CL_DIRECT_PF, true>(A, X, M, s + 2, lamh, lam, lamf, lamo, dtv);
+            ctstep<V, LIM, FT1, NU, 3, true, true, true, true, CL_DIRECT_PF, true>(A, X, M, s + 3, lamh, lam, lamf, lamo, dtv);
         }
     } else {
-        ctstep<V, LIM, FT1, 3, true, false, false, false, CL_MAPPED, false>(A, X, M, -1, lamh, lam, lamf, lamo);
-        ctstep<V, LIM, FT1, 0, true, true, false, false, CL_MAPPED, false>(A, X, M, 0, lamh, lam, lamf, lamo);
-        ctstep<V, LIM, FT1, 1, true, true, false, false, CL_MAPPED, false>(A, X, M, 1, lamh, lam, lamf, lamo);
-        ctstep<V, LIM, FT1, 2, true, true, false, false, CL_MAPPED, false>(A, X, M, 2, lamh, lam, lamf, lamo);
-        ctstep<V, LIM, FT1, 3, true, true, true, false, CL_MAPPED, true>(A, X, M, 3, lamh, lam, lamf, lamo);
+        ctstep<V, LIM, FT1, NU, 3, true, false, false, false, CL_MAPPED, false>(A, X, M, -1, lamh, lam, lamf, lamo, dtv);
+        ctstep<V, LIM, FT1, NU, 0, true, true, false, false, CL_MAPPED, false>(A, X, M, 0, lamh, lam, lamf, lamo, dtv);
+        ctstep<V, LIM, FT1, NU, 1, true, true, false, false, CL_MAPPED, false>(A, X, M, 1, lamh, lam, lamf, lamo, dtv);
+        ctstep<V, LIM, FT1, NU, 2, true, true, false, false, CL_MAPPED, false>(A, X, M, 2, lamh, lam, lamf, lamo, dtv);
+        ctstep<V, LIM, FT1, NU, 3, true, true, true, false, CL_MAPPED, true>(A, X, M, 3, lamh, lam, lamf, lamo, dtv);
     }
     // tail: cells s .. n+3 through the map (n-4 <= s <= n-1 after the loop,
     // s = 0 mod 4: at most eight cells)
-    if (s <= n + 3) ctstep<V, LIM, FT1, 0, true, true, true, true, CL_MAPPED, true>(A, X, M, s, lamh, lam, lamf, lamo);
-    if (s + 1 <= n + 3) ctstep<V, LIM, FT1, 1, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 1, lamh, lam, lamf, lamo);
-    if (s + 2 <= n + 3) ctstep<V, LIM, FT1, 2, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 2, lamh, lam, lamf, lamo);
-    if (s + 3 <= n + 3) ctstep<V, LIM, FT1, 3, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 3, lamh, lam, lamf, lamo);
-    if (s + 4 <= n + 3) ctstep<V, LIM, FT1, 0, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 4, lamh, lam, lamf, lamo);
-    if (s + 5 <= n + 3) ctstep<V, LIM, FT1, 1, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 5, lamh, lam, lamf, lamo);
-    if (s + 6 <= n + 3) ctstep<V, LIM, FT1, 2, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 6, lamh, lam, lamf, lamo);
-    if (s + 7 <= n + 3) ctstep<V, LIM, FT1, 3, true, true, true, true, CL_NONE, false>(A, X, M, s + 7, lamh, lam, lamf, lamo);
+    if (s <= n + 3) ctstep<V, LIM, FT1, NU, 0, true, true, true, true, CL_MAPPED, true>(A, X, M, s, lamh, lam, lamf, lamo, dtv);
+    if (s + 1 <= n + 3) ctstep<V, LIM, FT1, NU, 1, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 1, lamh, lam, lamf, lamo, dtv);
+    if (s + 2 <= n + 3) ctstep<V, LIM, FT1, NU, 2, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 2, lamh, lam, lamf, lamo, dtv);
+    if (s + 3 <= n + 3) ctstep<V, LIM, FT1, NU, 3, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 3, lamh, lam, lamf, lamo, dtv);
+    if (s + 4 <= n + 3) ctstep<V, LIM, FT1, NU, 0, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 4, lamh, lam, lamf, lamo, dtv);
+    if (s + 5 <= n + 3) ctstep<V, LIM, FT1, NU, 1, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 5, lamh, lam, lamf, lamo, dtv);
+    if (s + 6 <= n + 3) ctstep<V, LIM, FT1, NU, 2, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 6, lamh, lam, lamf, lamo, dtv);
+    if (s + 7 <= n + 3) ctstep<V, LIM, FT1, NU, 3, true, true, true, true, CL_NONE, false>(A, X, M, s + 7, lamh, lam, lamf, lamo, dtv);
 }
 
-template <class V, int LIM, bool FT1>
+template <class V, int LIM, bool FT1, bool NU = false>
 __global__ void __launch_bounds__(128, VT<V>::F64 ? 1 : FISH_CT_MINB) ct_col_kernel(const ColCTArgs<typename VT<V>::S> A)
 {
-    ct_columns<V, LIM, FT1>(A, ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31);
+    ct_columns<V, LIM, FT1, NU>(A, ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5, threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------

@@ -420,6 +420,7 @@ template <class T> struct CFLArgs {
     T gamma, gm1;
     unsigned long long *minbits;  // order-preserving bits of the positive minimum (double)
     unsigned *flags;
+    const T *w[3] = {nullptr, nullptr, nullptr};  // irregular mesh: cell widths per axis (eq0420)
 };
 
 // FP32 signal speeds along the three axes of one cell, sharing the
@@ -471,9 +472,19 @@ __global__ void __launch_bounds__(256) cfl_kernel(CFLArgs<T> A)
         const long long rbase = (long long)m * g.st[f1] + (long long)k * g.st[f2];
         const long long om = (long long)(gmap(m - 1, nm, g.bc) - m) * g.st[f1];
         const long long ok = (long long)(gmap(k - 1, ns, g.bc) - k) * g.st[f2];
+        if (A.w[0]) {
+            // irregular mesh: this row's widths along the two slower axes
+            rh[f1] = (float)(1.0 / (double)A.w[f1][m]);
+            rh[f2] = (float)(1.0 / (double)A.w[f2][k]);
+        }
         for (int f = threadIdx.x; f < nf; f += blockDim.x) {
             const long long idx = rbase + f;
             const long long ofm = (long long)(gmap(f - 1, nf, g.bc) - f);
+            int cc[3];
+            cc[f0] = f;
+            cc[f1] = m;
+            cc[f2] = k;
+            if (A.w[0]) rh[f0] = (float)(1.0 / (double)A.w[f0][f]);
             T bc[3];
             bc[f0] = T(0.5) * (__ldg(A.in[5 + f0] + idx + ofm) + __ldg(A.in[5 + f0] + idx));
             bc[f1] = T(0.5) * (__ldg(A.in[5 + f1] + idx + om) + __ldg(A.in[5 + f1] + idx));
@@ -487,7 +498,8 @@ __global__ void __launch_bounds__(256) cfl_kernel(CFLArgs<T> A)
                               __ldg(A.in[1 + t2] + idx), __ldg(A.in[4] + idx)};
                     T bb[3] = {bc[d], bc[t1], bc[t2]};
                     const T sp = signal_speed<T>(u, bb, A.gamma, A.gm1, flags);
-                    const double r = (double)(T(A.h[d]) / sp);
+                    const T hd = A.w[0] ? A.w[d][cc[d]] : T(A.h[d]);  // eq0420
+                    const double r = (double)(hd / sp);
                     best = r < best ? r : best;
                 }
             } else {
@@ -545,6 +557,9 @@ template <class T> struct DiagArgs {
     Geom g;
     double h[3];
     double *partial;  // [gridDim.x][9]
+    // irregular mesh: cell widths per axis; the sums are then volume-weighted
+    // in the kernel and the divergence takes each cell's own widths
+    const T *w[3] = {nullptr, nullptr, nullptr};
 };
 
 template <class T>
@@ -556,10 +571,16 @@ __global__ void __launch_bounds__(256) diag_kernel(DiagArgs<T> A)
     double dmax = 0.0;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
          idx += (long long)gridDim.x * blockDim.x) {
-#pragma unroll
-        for (int f = 0; f < 8; ++f) s[f] += (double)A.in[f][idx];
         int cc[3];
         coords_of(g, idx, cc);
+        if (A.w[0]) {
+            const double vol = (double)A.w[0][cc[0]] * (double)A.w[1][cc[1]] * (double)A.w[2][cc[2]];
+#pragma unroll
+            for (int f = 0; f < 8; ++f) s[f] += (double)A.in[f][idx] * vol;
+        } else {
+#pragma unroll
+            for (int f = 0; f < 8; ++f) s[f] += (double)A.in[f][idx];
+        }
         bool skip = false;
         if (g.bc == BC_OUTFLOW)
             for (int ax = 0; ax < 3; ++ax)
@@ -569,7 +590,8 @@ __global__ void __launch_bounds__(256) diag_kernel(DiagArgs<T> A)
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
                 const long long lo = idx + (long long)(gmap(cc[ax] - 1, g.n[ax], g.bc) - cc[ax]) * g.st[ax];
-                dv += ((double)A.in[5 + ax][idx] - (double)A.in[5 + ax][lo]) / A.h[ax];
+                const double hx = A.w[0] ? (double)A.w[ax][cc[ax]] : A.h[ax];
+                dv += ((double)A.in[5 + ax][idx] - (double)A.in[5 + ax][lo]) / hx;
             }
             dmax = fmax(dmax, fabs(dv));
         }
@@ -661,6 +683,7 @@ template <class T> struct GravArgs {
     long long N, sd;
     int n, bc;
     double h;
+    const T *wd = nullptr;  // irregular mesh: cell widths along d (centre span, reading C-26)
 };
 
 template <class T>
@@ -673,7 +696,9 @@ __global__ void __launch_bounds__(256) gravity_kernel(GravArgs<T> A)
         if constexpr (sizeof(T) == 8) {
             const long long ip = i + (long long)(gmap(s + 1, A.n, A.bc) - s) * A.sd;
             const long long im = i + (long long)(gmap(s - 1, A.n, A.bc) - s) * A.sd;
-            const double dphi = (A.phi[ip] - A.phi[im]) / (2.0 * A.h);
+            const double span = A.wd ? 0.5 * A.wd[gmap(s - 1, A.n, A.bc)] + A.wd[s] + 0.5 * A.wd[gmap(s + 1, A.n, A.bc)]
+                                     : 2.0 * A.h;
+            const double dphi = (A.phi[ip] - A.phi[im]) / span;
             const double rho = A.rho[i];
             const double mo = A.md[i];
             const double mn = mo - tau * rho * dphi;
@@ -683,7 +708,14 @@ __global__ void __launch_bounds__(256) gravity_kernel(GravArgs<T> A)
             float dm1;
             if (s > 0) dm1 = A.phi[i - A.sd];
             else dm1 = A.bc == BC_PERIODIC ? A.phi[i + (long long)(A.n - 1) * A.sd] : 0.0f;
-            const float dphi = (A.phi[i] + dm1) * (float)(0.5 / A.h);
+            float dphi;
+            if (A.wd) {
+                const float span = 0.5f * (float)A.wd[gmap(s - 1, A.n, A.bc)] + (float)A.wd[s] +
+                                   0.5f * (float)A.wd[gmap(s + 1, A.n, A.bc)];
+                dphi = (A.phi[i] + dm1) / span;
+            } else {
+                dphi = (A.phi[i] + dm1) * (float)(0.5 / A.h);
+            }
             const float rho = A.rho[i];
             const float mo = A.md[i];
             const float dm = -((float)tau * rho) * dphi;

@@ -61,11 +61,13 @@ template <class T> bool Launch<T>::fluid_fuses_cfl(const Geom &g, int d, int lim
 template <class T>
 cudaError_t Launch<T>::fluid(const T *const in[8], T *const out[5], const T *phi, const double *dt,
                              const Geom &g, int d, int lim, bool hse, double gamma, double alpha,
-                             const double h3[3], unsigned *flags, unsigned long long *cfl_min, cudaStream_t s)
+                             const double h3[3], unsigned *flags, unsigned long long *cfl_min, cudaStream_t s,
+                             const T *const *w3)
 {
     Frame F;
     if (!frame_of(g, d, F)) return cudaErrorInvalidValue;
-    if (cfl_min && !uses_pairs<T>(F, lim, hse)) return cudaErrorInvalidValue;
+    if (w3 && (!w3[0] || !w3[1] || !w3[2])) return cudaErrorInvalidValue;
+    if (cfl_min && (w3 || !uses_pairs<T>(F, lim, hse))) return cudaErrorInvalidValue;
     const double h = h3[d];
     ColFluidArgs<T> A;
     // FP32 orders the frame so that t1 is the fast axis (the formulas are
@@ -100,11 +102,13 @@ cudaError_t Launch<T>::fluid(const T *const in[8], T *const out[5], const T *phi
     A.rh[0] = T(1.0 / h3[d]);
     A.rh[1] = T(1.0 / h3[a1]);
     A.rh[2] = T(1.0 / h3[a2]);
+    A.wd = w3 ? w3[d] : nullptr;
     if constexpr (sizeof(T) == 8) {
         return col_fluid<double>(A, hse, F.ft1, s);
     } else {
         // two columns per thread (packed FP32x2) when the fast extent is even
-        if (uses_pairs<T>(F, lim, hse)) return col_fluid<P2>(A, hse, true, s);
+        // (uniform meshes)
+        if (!w3 && uses_pairs<T>(F, lim, hse)) return col_fluid<P2>(A, hse, true, s);
         return col_fluid<float>(A, hse, true, s);
     }
 }
@@ -112,11 +116,12 @@ cudaError_t Launch<T>::fluid(const T *const in[8], T *const out[5], const T *phi
 template <class T>
 cudaError_t Launch<T>::ct(const T *rho, const T *md, const T *const b[3], T *const bout[3],
                           const double *dt, const Geom &g, int d, int lim, const double h[3],
-                          unsigned *flags, cudaStream_t s)
+                          unsigned *flags, cudaStream_t s, const T *const *w3)
 {
     (void)flags;
     Frame F;
     if (!frame_of(g, d, F)) return cudaErrorInvalidValue;
+    if (w3 && (!w3[0] || !w3[1] || !w3[2])) return cudaErrorInvalidValue;
     ColCTArgs<T> A;
     A.rho = rho;
     A.md = md;
@@ -141,11 +146,16 @@ cudaError_t Launch<T>::ct(const T *rho, const T *md, const T *const b[3], T *con
     A.h = h[d];
     A.hf = h[F.fast];
     A.ho = h[F.other];
+    if (w3) {
+        A.wd = w3[d];
+        A.wf = w3[F.fast];
+        A.wo = w3[F.other];
+    }
     if constexpr (sizeof(T) == 8) {
         return col_ct<double>(A, F.ft1, s);
     } else {
 #ifdef FISH_CT_PAIRS
-        if (F.nf % 2 == 0 && lim != LIM_NONE) return col_ct<P2>(A, true, s);
+        if (!w3 && F.nf % 2 == 0 && lim != LIM_NONE) return col_ct<P2>(A, true, s);
 #endif
         return col_ct<float>(A, true, s);
     }
@@ -153,9 +163,11 @@ cudaError_t Launch<T>::ct(const T *rho, const T *md, const T *const b[3], T *con
 
 template <class T>
 cudaError_t Launch<T>::cfl(const T *const in[8], const Geom &g, const double h[3], double gamma,
-                           unsigned long long *minbits, unsigned *flags, cudaStream_t s)
+                           unsigned long long *minbits, unsigned *flags, cudaStream_t s, const T *const *w3)
 {
     CFLArgs<T> A;
+    if (w3)
+        for (int a = 0; a < 3; ++a) A.w[a] = w3[a];
     for (int f = 0; f < 8; ++f) A.in[f] = in[f];
     A.g = g;
     for (int f = 0; f < 3; ++f) A.h[f] = h[f];
@@ -172,9 +184,11 @@ cudaError_t Launch<T>::cfl(const T *const in[8], const Geom &g, const double h[3
 
 template <class T>
 cudaError_t Launch<T>::diag(const T *const in[8], const Geom &g, const double h[3], double *partial,
-                            int nblocks, cudaStream_t s)
+                            int nblocks, cudaStream_t s, const T *const *w3)
 {
     DiagArgs<T> A;
+    if (w3)
+        for (int a = 0; a < 3; ++a) A.w[a] = w3[a];
     for (int f = 0; f < 8; ++f) A.in[f] = in[f];
     A.g = g;
     for (int f = 0; f < 3; ++f) A.h[f] = h[f];
@@ -203,7 +217,7 @@ cudaError_t Launch<T>::transpose(const T *const src[8], T *const dst[8], int nf,
 
 template <class T>
 cudaError_t Launch<T>::gravity(T *const u[5], const T *phi, const double *dt, double frac, const Geom &g, int d,
-                               double h, cudaStream_t s)
+                               double h, cudaStream_t s, const T *wd)
 {
     if (!phi || d < 0 || d > 2) return cudaErrorInvalidValue;
     GravArgs<T> A;
@@ -218,6 +232,7 @@ cudaError_t Launch<T>::gravity(T *const u[5], const T *phi, const double *dt, do
     A.n = g.n[d];
     A.bc = g.bc;
     A.h = h;
+    A.wd = wd;
     unsigned gr = grid_for(A.N, 256);
     if (gr > 152u * 16u) gr = 152u * 16u;
     gravity_kernel<T><<<gr, 256, 0, s>>>(A);
