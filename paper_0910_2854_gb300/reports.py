@@ -11,6 +11,12 @@ on one GPU and printed as one JSON line each:
       and both throughputs.
   python -m paper_0910_2854_gb300.reports batch
       the seeded batch of 64 uneven boxes: autotuned choice and throughput.
+  python -m paper_0910_2854_gb300.reports validation <name> [n] [fp32|fp64]
+      one of the paper's validation problems (sedov, spherical_riemann,
+      magnetic_explosion, rotor, mhd_riemann_2d) at the paper's size (or n)
+      run to the paper's end time: value ranges against the printed ones,
+      and for the Sedov blast the shock radius against the self-similar
+      t^(2/5) law and the printed radius.
 
 Every step runs in the CUDA kernels behind the C ABI; the inputs are the
 seeded synthetic fields of ``workloads``.
@@ -124,10 +130,126 @@ def batch(k=0.5, steps=10):
     return out
 
 
+VALIDATION = {  # name: (generator, paper size, CFL number, limiter)
+    "sedov": (W.sedov, 256, 0.5, "vanleer"),
+    "spherical_riemann": (W.spherical_riemann, 256, 0.5, "vanleer"),
+    "magnetic_explosion": (W.magnetic_explosion, 256, 0.5, "minmod"),
+    "rotor": (W.rotor, 256, 0.5, "vanleer"),
+    "mhd_riemann_2d": (W.mhd_riemann_2d, 512, 0.5, "vanleer"),
+}
+
+
+class StoppedEarly(Exception):
+    """The run met a non-physical state before the end time."""
+
+    def __init__(self, t, steps, msg):
+        super().__init__(msg)
+        self.t, self.steps = t, steps
+
+
+def run_to(box, t_end, k, t=0.0, max_steps=200000):
+    """Double steps with the CFL time step of the current state, the last
+    one shortened to land on t_end; returns (t, double steps).  Raises
+    StoppedEarly (with the time reached) when the path reports a
+    non-physical state."""
+    from . import FISH_ERR_NONPHYSICAL, FishError
+    steps = 0
+    while t < t_end * (1.0 - 1e-12):
+        try:
+            dt = min(box.cfl_dt(k), 0.5 * (t_end - t))
+            box.step(dt)
+        except FishError as exc:
+            if exc.code != FISH_ERR_NONPHYSICAL:
+                raise
+            raise StoppedEarly(t, steps, str(exc)) from exc
+        t += 2.0 * dt
+        steps += 1
+        if steps > max_steps:
+            raise RuntimeError("time step collapsed")
+    return t, steps
+
+
+def field_ranges(st, gamma, bc):
+    """Ranges of density, gas pressure, magnetic energy b^2/2 and kinetic
+    energy rho v^2/2 (cell-centred b: mean of the two faces)."""
+    bcc = np.array(W.cell_centred(st[5:8], bc))
+    e_mag = 0.5 * np.sum(bcc ** 2, axis=0)
+    e_kin = 0.5 * np.sum(st[1:4] ** 2, axis=0) / st[0]
+    p = (gamma - 1.0) * (st[4] - e_kin - e_mag)
+    out = {}
+    for key, a in (("rho", st[0]), ("p", p), ("e_mag", e_mag), ("e_kin", e_kin)):
+        out[key] = (float(a.min()), float(a.max()))
+    return out
+
+
+def radial_profile(rho, h):
+    """Mean density in shells of width h about the box centre (cubic box)."""
+    n = rho.shape[-1]
+    c = (np.arange(n) + 0.5) * h - 0.5 * n * h
+    Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    k = np.minimum((r / h).astype(np.int64), n)
+    cnt = np.bincount(k.ravel(), minlength=n + 1)
+    tot = np.bincount(k.ravel(), weights=rho.ravel(), minlength=n + 1)
+    prof = tot / np.maximum(cnt, 1)
+    return (np.arange(n + 1) + 0.5) * h, prof
+
+
+def validation(name, n=None, precision="fp32"):
+    from . import FISH_LIM_MINMOD, FISH_LIM_VANLEER
+    gen, n0, k, lim = VALIDATION[name]
+    n = int(n or n0)
+    w = gen(n)
+    t_end = w.meta["t_end"]
+    box = Box(*w.dims, w.gamma, bc=w.bc, precision=precision, h=w.h,
+              limiter=FISH_LIM_MINMOD if lim == "minmod" else FISH_LIM_VANLEER)
+    box.set_state(w.state)
+    out = {"report": "validation", "problem": name, "n": n, "dims": list(w.dims), "precision": precision,
+           "cfl": k, "limiter": lim, "t_end": t_end}
+    t0 = time.time()
+    if name == "sedov":
+        # the self-similar radius grows as t^(2/5): compare t_end/4 and t_end
+        radii = []
+        t = 0.0
+        for tt in (0.25 * t_end, t_end):
+            t, _ = run_to(box, tt, k, t)
+            r, prof = radial_profile(box.get_state()[0], w.h[0])
+            i = int(np.argmax(prof))
+            radii.append(float(r[i]))
+            peak = float(prof[i])
+        out["shock_radius"] = {"t_end_over_4": radii[0], "t_end": radii[1], "ratio": radii[1] / radii[0],
+                               "self_similar_ratio": 4.0 ** 0.4, "printed_t_end": 0.45, "cell": w.h[0]}
+        out["peak_shell_density"] = peak
+        out["strong_shock_density"] = (w.gamma + 1.0) / (w.gamma - 1.0)
+    else:
+        try:
+            t, steps = run_to(box, t_end, k)
+            out["double_steps"] = steps
+        except StoppedEarly as exc:
+            out["stopped_early"] = {"t": exc.t, "double_steps": exc.steps, "error": str(exc)[:160]}
+            box.close()
+            out["wall_s"] = time.time() - t0
+            return out
+    st = box.get_state()
+    out["wall_s"] = time.time() - t0
+    out["ranges"] = field_ranges(st, w.gamma, w.bc)
+    if "ranges" in w.meta:
+        out["printed_ranges"] = w.meta["ranges"]
+    d = box.diagnostics()
+    out["max_div_b"] = float(d[8])
+    box.close()
+    return out
+
+
 def main(argv):
     what = argv[1] if len(argv) > 1 else "batch"
-    args = [int(a) for a in argv[2:]]
     t0 = time.time()
+    if what == "validation":
+        res = validation(argv[2], *(argv[3:4] or [None]), *(argv[4:5] or ["fp32"]))
+        res["wall_s_total"] = time.time() - t0
+        print(json.dumps(res), flush=True)
+        return
+    args = [int(a) for a in argv[2:]]
     res = {"polytrope": polytrope, "fp32_vs_fp64": fp32_vs_fp64, "batch": batch}[what](*args)
     res["wall_s"] = time.time() - t0
     print(json.dumps(res), flush=True)

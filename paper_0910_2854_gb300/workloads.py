@@ -537,3 +537,114 @@ def batch_box(kind, dims, axis):
         return Workload(kind, np.ascontiguousarray(st), w.gamma, tuple(h), BC_OUTFLOW,
                         meta={"axis": axis})
     return blast(nx, ny, nz)
+
+
+# --------------------------------------------------------------------------
+# the paper's other validation problems (Sec. 4): cell-centre sampling of the
+# printed initial conditions, uniform fields given on the faces
+# --------------------------------------------------------------------------
+
+def _cube(n, L=1.0):
+    xc, _, _, h = _grid(n, L)
+    Z, Y, X = np.meshgrid(xc, xc, xc, indexing="ij")
+    return X, Y, Z, h
+
+
+SEDOV_T_END = 1.7419e-4
+SEDOV_E_TOTAL = 3.0e5
+
+
+def sedov(n=256, E_total=SEDOV_E_TOTAL, e_out=1e-3, r_in=0.01, gamma=5.0 / 3.0):
+    """Sedov-Taylor blast on [0,1]^3 (Sec. 4, Sedov-Taylor blast wave): rho =
+    1, v = 0, b = 0, the energy E_total spread uniformly over the cells whose
+    centre lies within r_in of the box centre, specific internal energy
+    e_out elsewhere; outflow boundaries.  The printed e = 3e3 inside r < 0.01
+    is not consistent with the printed end state (shock at r ~ 0.45 at
+    t = 1.7419e-4); E_total = 3e5 is (reading of the garbled value)."""
+    X, Y, Z, h = _cube(n)
+    r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2)
+    inside = r < max(r_in, 0.5 * math.sqrt(3.0) * h * 1.0001)  # at least the central cells
+    ncell = int(inside.sum())
+    e_in = E_total / (ncell * h ** 3)  # energy per volume, rho = 1
+    p = np.where(inside, (gamma - 1.0) * e_in, (gamma - 1.0) * e_out)
+    one = np.ones(X.shape)
+    z = 0 * one
+    st = assemble(one, (z, z, z), p, (z, z, z), gamma, BC_OUTFLOW)
+    return Workload("sedov", st, gamma, (h, h, h), BC_OUTFLOW,
+                    meta={"t_end": SEDOV_T_END, "E": E_total, "cells_inside": ncell})
+
+
+def spherical_riemann(n=256, gamma=5.0 / 3.0, R=0.25):
+    """Spherical Sod problem on [0,1]^3 (Sec. 4, spherical Riemann problem):
+    rho = 0.125, p = 0.1 inside r < 0.25 of the centre, rho = 1, p = 1
+    outside, v = 0, b = 0; run to t = 0.09; outflow boundaries."""
+    X, Y, Z, h = _cube(n)
+    r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2)
+    rho = np.where(r < R, 0.125, 1.0)
+    p = np.where(r < R, 0.1, 1.0)
+    z = 0 * rho
+    st = assemble(rho, (z, z, z), p, (z, z, z), gamma, BC_OUTFLOW)
+    return Workload("spherical_riemann", st, gamma, (h, h, h), BC_OUTFLOW, meta={"t_end": 0.09})
+
+
+MAGNETIC_EXPLOSION_RANGES = {  # printed ranges at t = 0.03 (Sec. 4, magnetic explosion, 256^3)
+    "rho": (0.24, 2.17), "p": (0.25, 15.85), "e_mag": (7.66, 33.50), "e_kin": (0.0, 17.33)}
+
+
+def magnetic_explosion(n=256, gamma=5.0 / 3.0):
+    """Magnetic explosion on [0,1]^3 (Sec. 4): rho = 1, v = 0, p = 100 for
+    r < 0.1, p = 1 for r > 0.125, linear in r between; b = (7, 7, 0)/sqrt(2);
+    run to t = 0.03 with CFL 0.5 and the minmod limiter; outflow boundaries."""
+    X, Y, Z, h = _cube(n)
+    r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2)
+    p = np.where(r < 0.1, 100.0, np.where(r > 0.125, 1.0, 100.0 + (1.0 - 100.0) * (r - 0.1) / 0.025))
+    one = np.ones(X.shape)
+    b0 = 7.0 / math.sqrt(2.0)
+    st = assemble(one, (0 * one,) * 3, p, (b0 * one, b0 * one, 0 * one), gamma, BC_OUTFLOW)
+    return Workload("magnetic_explosion", st, gamma, (h, h, h), BC_OUTFLOW,
+                    meta={"t_end": 0.03, "cfl": 0.5, "limiter": "minmod", "ranges": MAGNETIC_EXPLOSION_RANGES})
+
+
+def rotor(n=256, gamma=1.4, r0=0.1, r1=0.115):
+    """First rotor problem (Sec. 4, the rotor problem) on [0,1]^2 x one
+    cell: rho = 10 and rigid rotation v = 2 (-(y-1/2), x-1/2)/r0 for r < r0,
+    the tapered profile f = (r1-r)/(r1-r0) for r0 < r < r1, rho = 1 at rest
+    beyond; p = 1, b = (5/sqrt(4 pi), 0, 0); run to t = 0.15; outflow
+    boundaries (none are printed: reading)."""
+    xc, _, _, h = _grid(n)
+    Y, X = np.meshgrid(xc, xc, indexing="ij")
+    dx, dy = X - 0.5, Y - 0.5
+    r = np.sqrt(dx * dx + dy * dy)
+    f = np.clip((r1 - r) / (r1 - r0), 0.0, 1.0)
+    rho = np.where(r < r0, 10.0, np.where(r < r1, 1.0 + 9.0 * f, 1.0))
+    rs = np.maximum(r, 1e-300)
+    vx = np.where(r < r0, -2.0 * dy / r0, np.where(r < r1, -2.0 * f * dy / rs, 0.0))
+    vy = np.where(r < r0, 2.0 * dx / r0, np.where(r < r1, 2.0 * f * dx / rs, 0.0))
+    rho, vx, vy = rho[None], vx[None], vy[None]
+    one = np.ones(rho.shape)
+    st = assemble(rho, (vx, vy, 0 * one), 1.0, (5.0 / math.sqrt(4.0 * math.pi) * one, 0 * one, 0 * one),
+                  gamma, BC_OUTFLOW)
+    return Workload("rotor", st, gamma, (h, h, h), BC_OUTFLOW, meta={"t_end": 0.15})
+
+
+MHD_RIEMANN_2D_RANGES = {  # printed ranges at t = 0.8 (Sec. 4, two-dimensional MHD Riemann problem, 512^2)
+    "rho": (0.3428, 2.5698), "p": (0.1208, 0.7757), "e_mag": (0.0039, 0.2953), "e_kin": (0.0, 0.6233)}
+
+
+def mhd_riemann_2d(n=512, L=0.8, gamma=5.0 / 3.0):
+    """Two-dimensional MHD Riemann problem (Sec. 4) on [0,0.8]^2 x one cell:
+    four quadrant states (rho, v_x, v_y, v_z, p) as printed, uniform
+    b = (2, 0, 1)/sqrt(4 pi); zeroth-order extrapolation boundaries; run to
+    t = 0.8."""
+    xc, _, _, h = _grid(n, L)
+    Y, X = np.meshgrid(xc, xc, indexing="ij")
+    left, low = X <= L / 2, Y <= L / 2
+    rho = np.where(low, np.where(left, 1.0, 3.0), np.where(left, 2.0, 1.0))
+    vx = np.where(low, -0.75, 0.75)
+    vy = np.where(left, 0.5, -0.5)
+    rho, vx, vy = rho[None], vx[None], vy[None]
+    one = np.ones(rho.shape)
+    s = 1.0 / math.sqrt(4.0 * math.pi)
+    st = assemble(rho, (vx, vy, 0 * one), 1.0, (2.0 * s * one, 0 * one, s * one), gamma, BC_OUTFLOW)
+    return Workload("mhd_riemann_2d", st, gamma, (h, h, h), BC_OUTFLOW,
+                    meta={"t_end": 0.8, "ranges": MHD_RIEMANN_2D_RANGES})
