@@ -14,23 +14,28 @@ static inline unsigned col_grid(long long work, int block)
     return (unsigned)(g < 1 ? 1 : g);
 }
 
+// blocks of fluid_col_kernel: one thread per column group
+template <class V> static unsigned fluid_blocks(const ColFluidArgs<typename VT<V>::S> &A)
+{
+    return col_grid((long long)(A.nf / VT<V>::W) * A.no, 128);
+}
+
 template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool NU = false>
 static cudaError_t col_fluid_launch(const ColFluidArgs<typename VT<V>::S> &A, cudaStream_t s)
 {
-    const long long cols = (long long)(A.nf / VT<V>::W) * A.no;
     if constexpr (NU) {
         if (A.cfl_min) return cudaErrorInvalidValue;
-        fluid_col_kernel<V, HSE, GRAV, LIM, FT1, false, true><<<col_grid(cols, 128), 128, 0, s>>>(A);
+        fluid_col_kernel<V, HSE, GRAV, LIM, FT1, false, true><<<fluid_blocks<V>(A), 128, 0, s>>>(A);
         return cudaGetLastError();
     }
     if constexpr (std::is_same<V, P2>::value && !HSE) {
         if (A.cfl_min) {
-            fluid_col_kernel<V, HSE, GRAV, LIM, FT1, true><<<col_grid(cols, 128), 128, 0, s>>>(A);
+            fluid_col_kernel<V, HSE, GRAV, LIM, FT1, true><<<fluid_blocks<V>(A), 128, 0, s>>>(A);
             return cudaGetLastError();
         }
     }
     if (A.cfl_min) return cudaErrorInvalidValue;  // only the two-column kernels carry the CFL epilogue
-    fluid_col_kernel<V, HSE, GRAV, LIM, FT1><<<col_grid(cols, 128), 128, 0, s>>>(A);
+    fluid_col_kernel<V, HSE, GRAV, LIM, FT1><<<fluid_blocks<V>(A), 128, 0, s>>>(A);
     return cudaGetLastError();
 }
 
@@ -79,10 +84,11 @@ cudaError_t col_fluid(const ColFluidArgs<typename VT<V>::S> &A, bool hse, bool f
 template <class V, int LIM, bool FT1, bool NU = false>
 static cudaError_t col_ct_launch(const ColCTArgs<typename VT<V>::S> &A, cudaStream_t s)
 {
-    // one warp per 31 W columns of a row (plus a halo lane)
+    // one warp per 31 W columns of a row (plus a halo lane); a block takes
+    // one segment of four consecutive rows
     const int segc = 31 * VT<V>::W;
-    const long long warps = (long long)((A.nf + segc - 1) / segc) * A.no;
-    ct_col_kernel<V, LIM, FT1, NU><<<col_grid(warps * 32, 128), 128, 0, s>>>(A);
+    const long long blocks = (long long)((A.nf + segc - 1) / segc) * ((A.no + 3) / 4);
+    ct_col_kernel<V, LIM, FT1, NU><<<(unsigned)blocks, 128, 0, s>>>(A);
     return cudaGetLastError();
 }
 
