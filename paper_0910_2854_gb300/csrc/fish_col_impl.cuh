@@ -85,10 +85,10 @@ template <class V, int LIM, bool FT1, bool NU = false>
 static cudaError_t col_ct_launch(const ColCTArgs<typename VT<V>::S> &A, cudaStream_t s)
 {
     // one warp per 31 W columns of a row (plus a halo lane); a block takes
-    // one segment of four consecutive rows
+    // one segment of FISH_CT_ROWS consecutive rows
     const int segc = 31 * VT<V>::W;
-    const long long blocks = (long long)((A.nf + segc - 1) / segc) * ((A.no + 3) / 4);
-    ct_col_kernel<V, LIM, FT1, NU><<<(unsigned)blocks, 128, 0, s>>>(A);
+    const long long blocks = (long long)((A.nf + segc - 1) / segc) * ((A.no + FISH_CT_ROWS - 1) / FISH_CT_ROWS);
+    ct_col_kernel<V, LIM, FT1, NU><<<(unsigned)blocks, 32 * FISH_CT_ROWS, 0, s>>>(A);
     return cudaGetLastError();
 }
 

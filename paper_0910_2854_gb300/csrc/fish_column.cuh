@@ -1135,16 +1135,21 @@ __device__ __forceinline__ void ct_columns(const ColCTArgs<typename VT<V>::S> &A
     if (s + 7 <= n + 3) ctstep<V, LIM, FT1, NU, 3, true, true, true, true, CL_NONE, false>(A, X, M, s + 7, lamh, lam, lamf, lamo, dtv);
 }
 
-// The four warps of a block take the same segment of four consecutive rows
-// of the other axis, so the neighbour-row loads of each warp (rho, m_d of
-// rows o-1 and o+1, the other-axis face of row o-1) are mostly the own-row
-// loads of its sibling warps, served from L1.  Grid: segments x ceil(no/4).
+// The warps of a block take the same segment of FISH_CT_ROWS consecutive
+// rows of the other axis, so the neighbour-row loads of each warp (rho, m_d
+// of rows o-1 and o+1, the other-axis face of row o-1) are mostly the
+// own-row loads of its sibling warps, served from L1.  Grid: segments x
+// ceil(no/FISH_CT_ROWS).
+#ifndef FISH_CT_ROWS
+#define FISH_CT_ROWS 8   // rows (warps) per CT block
+#endif
 template <class V, int LIM, bool FT1, bool NU = false>
-__global__ void __launch_bounds__(128, VT<V>::F64 ? 1 : FISH_CT_MINB) ct_col_kernel(const ColCTArgs<typename VT<V>::S> A)
+__global__ void __launch_bounds__(32 * FISH_CT_ROWS, VT<V>::F64 ? 1 : FISH_CT_MINB * 4 / FISH_CT_ROWS)
+    ct_col_kernel(const ColCTArgs<typename VT<V>::S> A)
 {
     constexpr int SEGC = 31 * VT<V>::W;
     const long long nseg = (A.nf + SEGC - 1) / SEGC;
-    const long long seg = blockIdx.x % nseg, ob = (blockIdx.x / nseg) * 4 + (threadIdx.x >> 5);
+    const long long seg = blockIdx.x % nseg, ob = (blockIdx.x / nseg) * FISH_CT_ROWS + (threadIdx.x >> 5);
     ct_columns<V, LIM, FT1, NU>(A, ob * nseg + seg, threadIdx.x & 31);
 }
 
