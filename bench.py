@@ -239,7 +239,7 @@ def time_operators(F, box, torch, reps=3):
 # capture summarised in profiles/sweeps_f32_turbulence_384.md (384^3 launch,
 # dram__bytes_read.sum + dram__bytes_write.sum over its cells).  Set an entry
 # to None when that kernel changes until it is captured again.
-TRAFFIC_B_PER_CELL = {"fluid": 52.2, "ct": None}
+TRAFFIC_B_PER_CELL = {"fluid": 52.2, "ct": 32.1}
 
 
 def traffic_per_cell(kernel_key):
