@@ -916,20 +916,30 @@ __device__ __forceinline__ void ctload(const ColCTArgs<typename VT<V>::S> &A, co
     if constexpr (OUTLD) R.bdo = vload<V>(A.bd, X.base + (long long)(MAPPED ? min(s - 4, A.n - 1) : s - 4) * A.sd);
 }
 
-// prefetch into L2 the fields of interior cell i
+// prefetch into L2 the fields of interior cell i (the neighbour rows too
+// with FISH_CT_PF_NEIGH: with the warps of a block on consecutive rows they
+// are mostly the own rows of sibling warps)
+#ifndef FISH_CT_PF_DIST
+#define FISH_CT_PF_DIST 1
+#endif
+#ifndef FISH_CT_PF_NEIGH
+#define FISH_CT_PF_NEIGH 1
+#endif
 template <class V>
 __device__ __forceinline__ void ctprefetch(const ColCTArgs<typename VT<V>::S> &A, const CTCtx<typename VT<V>::S> &X,
                                            long long i)
 {
     pf_l2(A.rho + i);
     pf_l2(A.md + i);
+#if FISH_CT_PF_NEIGH
     pf_l2(A.rho + i + X.oom);
     pf_l2(A.md + i + X.oom);
     pf_l2(A.rho + i + X.oop);
     pf_l2(A.md + i + X.oop);
+    pf_l2(A.bo + i + X.oom);
+#endif
     pf_l2(A.bf + i);
     pf_l2(A.bo + i);
-    pf_l2(A.bo + i + X.oom);
     pf_l2(A.bd + i);
 }
 
@@ -979,7 +989,7 @@ __device__ __forceinline__ void ctstep(const ColCTArgs<typename VT<V>::S> &A, co
     if constexpr (LD == CL_DIRECT || LD == CL_DIRECT_PF) {
         ctload<V, false, NOUT, NU>(A, X, s + 1, M.R);
         if constexpr (LD == CL_DIRECT_PF)
-            ctprefetch<V>(A, X, X.base + (long long)min(s + 1 + FISH_PF_DIST, A.n - 1) * A.sd);
+            ctprefetch<V>(A, X, X.base + (long long)min(s + 1 + FISH_CT_PF_DIST, A.n - 1) * A.sd);
     } else if constexpr (LD == CL_MAPPED) {
         ctload<V, true, NOUT, NU>(A, X, s + 1, M.R);
     }
