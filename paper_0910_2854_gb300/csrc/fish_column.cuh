@@ -464,6 +464,9 @@ __device__ __forceinline__ void fload_direct(const ColFluidArgs<typename VT<V>::
 #define FISH_PF_DIST 2
 #endif
 
+#ifndef FISH_FL_PF_NEIGH
+#define FISH_FL_PF_NEIGH 1   // also the lower other-axis face (a neighbour row)
+#endif
 // prefetch into L2 the fields the fluid march will load for interior cell i
 template <class V, bool GRAV, bool FT1>
 __device__ __forceinline__ void fprefetch(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S> &X,
@@ -476,7 +479,9 @@ __device__ __forceinline__ void fprefetch(const ColFluidArgs<typename VT<V>::S> 
     pf_l2(A.bd + i);
     pf_l2(bfp + i);
     pf_l2(bop + i);
+#if FISH_FL_PF_NEIGH
     pf_l2(bop + i + X.oom);
+#endif
     if (GRAV) pf_l2(A.phi + i);
 }
 

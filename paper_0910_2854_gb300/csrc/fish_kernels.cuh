@@ -240,21 +240,28 @@ template <class T> struct TransArgs {
     long long plane;     // elements per z-plane
 };
 
-// Tiles of 64 source rows x 32 elements: a thread keeps eight loads in
-// flight, and the loads of field f+1 are issued before field f is stored
-// (two tiles, one barrier per field: a tile is rewritten two fields later,
-// after every thread has passed the barrier between).
+// Tiles of FISH_TR_ROWS source rows x 32 elements: a thread keeps
+// FISH_TR_ROWS/8 loads in flight, and the loads of field f+1 are issued
+// before field f is stored (two tiles, one barrier per field: a tile is
+// rewritten two fields later, after every thread has passed the barrier
+// between).
+#ifndef FISH_TR_ROWS
+#define FISH_TR_ROWS 64
+#endif
+// tile height: FP64 tiles stay within the 48 KB of static shared memory
+template <class T> constexpr int tr_rows() { return sizeof(T) == 8 && FISH_TR_ROWS > 64 ? 64 : FISH_TR_ROWS; }
 template <class T>
 __global__ void __launch_bounds__(256) transpose_kernel(TransArgs<T> A)
 {
-    __shared__ T tile[2][64][33];
-    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 64;
+    constexpr int TR = tr_rows<T>(), KL = TR / 8;
+    __shared__ T tile[2][TR][33];
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * TR;
     const long long zoff = (long long)blockIdx.z * A.plane;
     const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
     const int rl = r0 + tx;
-    T v[8];
+    T v[KL];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < KL; ++k) {
         const int c = c0 + ty + 8 * k;
         v[k] = (rl < A.nr && c < A.nc) ? A.src[0][zoff + (long long)c * A.nr + rl] : T(0);
     }
@@ -262,20 +269,20 @@ __global__ void __launch_bounds__(256) transpose_kernel(TransArgs<T> A)
     for (int f = 0; f < A.nf; ++f) {
         const int b = f & 1;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) tile[b][ty + 8 * k][tx] = v[k];
+        for (int k = 0; k < KL; ++k) tile[b][ty + 8 * k][tx] = v[k];
         __syncthreads();
         if (f + 1 < A.nf) {
             const T *__restrict__ src = A.src[f + 1] + zoff;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
+            for (int k = 0; k < KL; ++k) {
                 const int c = c0 + ty + 8 * k;
                 v[k] = (rl < A.nr && c < A.nc) ? src[(long long)c * A.nr + rl] : T(0);
             }
         }
         T *__restrict__ dst = A.dst[f] + zoff;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int idx = ty + 8 * k;  // 0 .. 63: destination row r0 + (idx & 31), column half idx >> 5
+        for (int k = 0; k < KL; ++k) {
+            const int idx = ty + 8 * k;  // destination row r0 + (idx & 31), column block idx >> 5
             const int r = r0 + (idx & 31), cl = tx + 32 * (idx >> 5), c = c0 + cl;
             if (r < A.nr && c < A.nc) dst[(long long)r * A.nc + c] = tile[b][cl][idx & 31];
         }

@@ -210,7 +210,7 @@ cudaError_t Launch<T>::transpose(const T *const src[8], T *const dst[8], int nf,
     A.nr = nr;
     A.nc = nc;
     A.plane = (long long)nr * nc;
-    dim3 grid((nr + 31) / 32, (nc + 63) / 64, nz);
+    dim3 grid((nr + 31) / 32, (nc + tr_rows<T>() - 1) / tr_rows<T>(), nz);
     transpose_kernel<T><<<grid, dim3(32, 8), 0, s>>>(A);
     return cudaGetLastError();
 }
