@@ -242,6 +242,14 @@ def time_operators(F, box, torch, reps=3):
 TRAFFIC_B_PER_CELL = {"fluid": 52.2, "ct": 32.1}
 
 
+# FP64 pipe instructions (DADD + DMUL + DFMA, thread level) per cell of one
+# launch of each FP64 kernel kind, from the ncu capture summarised in
+# profiles/sweeps_f64_orszag_tang_128.md (Orszag-Tang 128^3).  The FP64 path
+# is bound by GB300's FP64 pipe, so its roofline is this rate against the
+# probed FMA rate of the device (fish_probe_fp64_fma).
+FP64_OPS_PER_CELL = {"fluid": 537, "ct": 170}
+
+
 def traffic_per_cell(kernel_key):
     return TRAFFIC_B_PER_CELL.get(kernel_key.split("_")[0])
 
@@ -327,9 +335,18 @@ def run_fish(args, rank, world, local):
             b64 = make_box(F, W, FP64_WORKLOAD, FP64_WORKLOAD["n"], torch)
             ms64, _ = time_steps(b64, torch, max(3, min(args.steps, 10)), args.warmup)
             k64 = max(3, min(args.steps, 10))
-            v64 = FP64_WORKLOAD["n"] ** 3 / (ms64 / k64 * 1e-3)
+            n64 = FP64_WORKLOAD["n"] ** 3
+            v64 = n64 / (ms64 / k64 * 1e-3)
+            ops64 = time_operators(F, b64, torch)
+            key64 = max(ops64, key=ops64.get)
+            peak64 = F.probe_fp64_fma()
+            ach64 = FP64_OPS_PER_CELL[key64.split("_")[0]] * n64 / (ops64[key64] * 1e-3)
             fp64 = {"workload": FP64_WORKLOAD["workload"], "value": v64, "unit": UNIT, "ms_per_step": ms64 / k64,
-                    "fp32_over_fp64": (value / world) / v64}
+                    "fp32_over_fp64": (value / world) / v64,
+                    "roofline": {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "FP64 pipe op/s",
+                                 "frac": ach64 / peak64, "kernel": key64, "kernel_ms": ops64[key64],
+                                 "ops_per_cell": FP64_OPS_PER_CELL[key64.split("_")[0]],
+                                 "peak_source": "probed (fish_probe_fp64_fma)", "op_ms": ops64}}
             b64.close()
         batch = None
         if not args.no_batch:

@@ -179,6 +179,15 @@ const char *fish_last_error(fish_ctx *ctx);
 /* Number of kernel launches queued by this context since creation. */
 long long fish_launch_count(fish_ctx *ctx);
 
+/* Measurement helper with no counterpart in the paper: the FP64 pipe
+ * throughput of the current device in fused multiply-adds per second
+ * (each thread of sms x 8 blocks of 256 runs eight independent FMA chains;
+ * three timed launches after one warm-up).  It is the peak the FP64 sweeps
+ * are compared against, since GB300's FP64 rate is far below its bandwidth.
+ * Allocates and frees its own scratch; synchronous.  FISH_ERR_ARG on a NULL
+ * output, FISH_ERR_CUDA if any CUDA call fails (*fma_per_s is then 0). */
+int fish_probe_fp64_fma(double *fma_per_s);
+
 /* ---- batches of independent boxes (FP32) ---------------------------------
  * Many boxes of uneven sizes advanced together: every sweep of every box is
  * one persistent launch over a device work queue, each box keeps its own CFL

@@ -35,7 +35,7 @@ EXPORTS = ("fish_create", "fish_set_option", "fish_set_stream", "fish_set_alloca
            "fish_set_state_device", "fish_set_state_host", "fish_set_potential", "fish_set_mesh", "fish_cfl_dt", "fish_step", "fish_step_cfl",
            "fish_last_dt", "fish_apply", "fish_get_state", "fish_get_state_device", "fish_diagnostics",
            "fish_sync", "fish_clear_error", "fish_last_error", "fish_launch_count", "fish_destroy",
-           "fish_diagnostics_noalloc", "fish_batch_create", "fish_batch_set_option", "fish_batch_set_stream",
+           "fish_diagnostics_noalloc", "fish_probe_fp64_fma", "fish_batch_create", "fish_batch_set_option", "fish_batch_set_stream",
            "fish_batch_set_state", "fish_batch_step", "fish_batch_get_state", "fish_batch_last_dt",
            "fish_batch_sync", "fish_batch_last_error", "fish_batch_launch_count", "fish_batch_cells",
            "fish_batch_destroy")
@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH):
             "fish_set_state_device": ([P, P, ctypes.c_int], ctypes.c_int),
             "fish_set_state_host": ([P, P, ctypes.c_int], ctypes.c_int),
             "fish_set_potential": ([P, D], ctypes.c_int),
+            "fish_probe_fp64_fma": ([D], ctypes.c_int),
             "fish_set_mesh": ([P, D, D, D], ctypes.c_int),
             "fish_cfl_dt": ([P, ctypes.c_double, D], ctypes.c_int),
             "fish_step": ([P, ctypes.c_double], ctypes.c_int),
@@ -435,3 +436,14 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def probe_fp64_fma():
+    """FP64 fused multiply-adds per second of the current device (the peak
+    the FP64 sweeps are compared against)."""
+    lib = load()
+    out = ctypes.c_double()
+    code = lib.fish_probe_fp64_fma(ctypes.byref(out))
+    if code != FISH_OK:
+        raise FishError(code, "fish_probe_fp64_fma failed")
+    return out.value

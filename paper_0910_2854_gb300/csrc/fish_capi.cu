@@ -911,6 +911,42 @@ const char *fish_last_error(fish_ctx *c) { return c ? c->err.c_str() : "null con
 
 long long fish_launch_count(fish_ctx *c) { return c ? c->launches : -1; }
 
+int fish_probe_fp64_fma(double *fma_per_s)
+{
+    if (!fma_per_s) return FISH_ERR_ARG;
+    *fma_per_s = 0.0;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess) {
+        (void)cudaGetLastError();
+        return FISH_ERR_CUDA;
+    }
+    const int blocks = sms * 8, iters = 4096;
+    double *buf = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = FISH_ERR_CUDA;
+    float ms = 0.0f;
+    if (cudaMalloc(&buf, (size_t)blocks * 256 * sizeof(double)) != cudaSuccess) goto done;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) goto done;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) goto done;
+    if (fish::launch_dfma_probe(buf, blocks, iters, s) != cudaSuccess) goto done;  // warm-up
+    if (cudaEventRecord(e0, s) != cudaSuccess) goto done;
+    for (int r = 0; r < 3; ++r)
+        if (fish::launch_dfma_probe(buf, blocks, iters, s) != cudaSuccess) goto done;
+    if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) goto done;
+    if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || !(ms > 0.0f)) goto done;
+    *fma_per_s = 3.0 * (double)blocks * 256.0 * 8.0 * iters / (ms * 1e-3);
+    rc = FISH_OK;
+done:
+    if (rc != FISH_OK) (void)cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    if (buf) cudaFree(buf);
+    return rc;
+}
+
 void fish_destroy(fish_ctx *c)
 {
     if (!c) return;

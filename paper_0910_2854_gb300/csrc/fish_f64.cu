@@ -31,4 +31,32 @@ cudaError_t launch_set_scalar(double *p, double v, cudaStream_t s)
     set_scalar_kernel<<<1, 1, 0, s>>>(p, v);
     return cudaGetLastError();
 }
+
+// FP64 pipe throughput probe: every thread runs eight independent chains of
+// fused multiply-adds (x <- x a + b, |a| < 1, so the chains stay bounded) and
+// writes its sum, so nothing is optimised away.  The FP64 sweeps are
+// compared against this rate (their DADD, DMUL and DFMA each take one issue
+// of the FP64 pipe).
+static __global__ void __launch_bounds__(256) dfma_probe_kernel(double *out, int iters, double a, double b)
+{
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+#pragma unroll 1
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = __fma_rn(x[k], a, b);
+    }
+    double sum = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sum += x[k];
+    out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
+cudaError_t launch_dfma_probe(double *out, int blocks, int iters, cudaStream_t s)
+{
+    dfma_probe_kernel<<<blocks, 256, 0, s>>>(out, iters, 0.9999999, 1e-7);
+    return cudaGetLastError();
+}
 }  // namespace fish
+

@@ -49,5 +49,7 @@ cudaError_t launch_cfl_finish(unsigned long long *minbits, double k, double *dt,
 cudaError_t launch_set_scalar(double *p, double v, cudaStream_t s);
 // reset a CFL minimum to +infinity before a reduction
 cudaError_t launch_reset_min(unsigned long long *minbits, cudaStream_t s);
+// FP64 pipe probe: blocks x 256 threads, each 8 x iters fused multiply-adds
+cudaError_t launch_dfma_probe(double *out, int blocks, int iters, cudaStream_t s);
 
 }  // namespace fish

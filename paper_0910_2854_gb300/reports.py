@@ -11,6 +11,10 @@ on one GPU and printed as one JSON line each:
       and both throughputs.
   python -m paper_0910_2854_gb300.reports batch
       the seeded batch of 64 uneven boxes: autotuned choice and throughput.
+  python -m paper_0910_2854_gb300.reports fp64_sweeps [n]
+      the FP64 path on the Orszag-Tang box n^3: one double step and each
+      operator timed with CUDA events, next to the probed FP64 FMA rate of
+      the device.
   python -m paper_0910_2854_gb300.reports validation <name> [n] [fp32|fp64]
       one of the paper's validation problems (sedov, spherical_riemann,
       magnetic_explosion, rotor, mhd_riemann_2d) at the paper's size (or n)
@@ -97,6 +101,34 @@ def fp32_vs_fp64(n=1024, steps=20, k=0.5):
     d = (rho["fp32"] - rho["fp64"]).abs().mean().item() / rho["fp64"].abs().mean().item()
     out["l1_rho_rel"] = d
     out["fp32_over_fp64"] = out["fp32"]["cell_updates_per_s"] / out["fp64"]["cell_updates_per_s"]
+    return out
+
+
+def fp64_sweeps(n=128, steps=3, k=0.5):
+    import torch
+    from . import FISH_OP_CT, FISH_OP_FLUID, probe_fp64_fma
+    w = W.orszag_tang(n)
+    box = Box(n, n, n, w.gamma, precision="fp64", h=w.h)
+    box.set_state(w.state)
+    box.step_cfl(k, 1)
+    box.sync()
+    ms = _timed_steps(box, torch, k, steps)
+    dt = box.cfl_dt(k)
+    out = {"report": "fp64_sweeps", "n": n, "ms_per_step": ms / steps}
+    for kind, op in (("fluid", FISH_OP_FLUID), ("ct", FISH_OP_CT)):
+        for d in range(3):
+            box.apply(op, d, dt)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(box.stream)
+            for _ in range(2):
+                box.apply(op, d, dt)
+            e1.record(box.stream)
+            e1.synchronize()
+            out["%s_%s_ms" % (kind, "xyz"[d])] = e0.elapsed_time(e1) / 2
+    box.sync()
+    box.close()
+    out["fp64_fma_per_s"] = probe_fp64_fma()
     return out
 
 
@@ -250,7 +282,8 @@ def main(argv):
         print(json.dumps(res), flush=True)
         return
     args = [int(a) for a in argv[2:]]
-    res = {"polytrope": polytrope, "fp32_vs_fp64": fp32_vs_fp64, "batch": batch}[what](*args)
+    res = {"polytrope": polytrope, "fp32_vs_fp64": fp32_vs_fp64, "batch": batch,
+           "fp64_sweeps": fp64_sweeps}[what](*args)
     res["wall_s"] = time.time() - t0
     print(json.dumps(res), flush=True)
 

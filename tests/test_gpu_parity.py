@@ -539,3 +539,10 @@ def test_irregular_mesh_rejects_bad_widths(F):
         gb.set_mesh([np.array([0.25, 0.25, -0.25, 0.25]), None, None])
     assert ei.value.code == F.FISH_ERR_ARG
     gb.close()
+
+
+def test_fp64_fma_probe(F):
+    """The FP64 pipe probe returns a positive rate below the device's FP32
+    FMA rate bound (152 SMs x 128 lanes x 2.1 GHz)."""
+    r = F.probe_fp64_fma()
+    assert 1e9 < r < 152 * 128 * 2.1e9
