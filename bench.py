@@ -66,6 +66,9 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--oracle-sample", type=float, default=None,
+                   help="print only the oracle's rate on the 128^3 twin within this many seconds (the "
+                        "single-core leg runs itself this way with OMP_NUM_THREADS=1)")
     return p.parse_args()
 
 
@@ -148,6 +151,16 @@ def oracle_rate(n_twin=128, budget_s=10.0, min_steps=1, max_steps=50):
     el = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return w.ncells * steps / el, steps, el, cores, w.ncells
+
+
+def oracle_rate_single_core(budget_s=8.0):
+    """The same oracle sample on one host core (a child process with
+    OMP_NUM_THREADS=1, so the OpenMP runtime of this process is untouched)."""
+    import subprocess
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(budget_s)],
+                         env=env, capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
 
 
 def run_reference(args, rank, world):
@@ -363,6 +376,10 @@ def run_fish(args, rank, world, local):
             cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": "%d double steps (%.1f s) of the 128^3 twin (%d cells) of the workload"
                              % (steps, el, cells)}
+            try:
+                cpu["single_core"] = oracle_rate_single_core(8.0)
+            except Exception as exc:  # report, do not hide
+                cpu["single_core"] = {"error": repr(exc)[:200]}
         result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                   "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                   "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded, generated on the device)",
@@ -385,6 +402,10 @@ def run_fish(args, rank, world, local):
 
 def main():
     args = parse()
+    if args.oracle_sample is not None:
+        rate, steps, el, cores, cells = oracle_rate(128, budget_s=args.oracle_sample)
+        print(json.dumps({"value": rate, "unit": UNIT, "cores": cores, "steps": steps, "seconds": el}))
+        return 0
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
