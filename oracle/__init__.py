@@ -26,6 +26,14 @@ Parity status of the functions (what pins each one; see ``tests/test_oracle_*``)
   * operator-split gravity (``gravity_split=True``): pinned by the exact
     impulse and kinetic-energy change of a uniform state in a linear
     potential.
+  * irregular Cartesian meshes (``widths=``): pinned by equal widths giving
+    the uniform method to round-off, conservation of the volume-weighted
+    totals and of the per-cell-width divergence, a uniform state staying
+    uniform, exact free fall in a linear potential (split and unsplit), the
+    commutation with a reflection of state and mesh, exact shear-flow face
+    velocities and the closed-form CFL step.  Parity unpinned: the weights
+    of the edge-velocity interpolation along the sweep (they only decide the
+    upwind side where the smoothed face velocity changes sign).
   * ``test_oracle_mutants.py`` plants mistakes in a copy of the source and
     checks that the pins catch each of them.
 """
