@@ -182,7 +182,7 @@ def run_reference(args, rank, world):
     value = w.ncells * args.steps / el
     cfg = {"workload": WORKLOAD["workload"], "sample": "%d^3 twin of the workload" % sample,
            "precision": "fp64 (oracle)", "cfl": CFL}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
             "config": cfg, "impl": "reference",

@@ -1,0 +1,41 @@
+"""The JSON line of bench.py: the reference arm (the CPU oracle) on CPU, and
+the GPU arm on a small box, each with every key the line must carry."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+BASE_KEYS = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+             "vs_baseline", "dtype", "data", "config", "e2e", "cpu_baseline"}
+
+
+def run_bench(*args, timeout=900):
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], cwd=ROOT, capture_output=True,
+                         text=True, timeout=timeout, check=True)
+    lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, out.stdout
+    return json.loads(lines[0])
+
+
+def test_reference_arm_line():
+    d = run_bench("--impl", "reference", "--steps", "1", "--warmup", "1", "--n", "24")
+    assert BASE_KEYS <= set(d)
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+@pytest.mark.gpu
+def test_gpu_arm_line():
+    d = run_bench("--n", "64", "--steps", "3", "--warmup", "3", "--no-batch", "--no-fp64", "--no-cpu-baseline")
+    assert BASE_KEYS <= set(d) and {"roofline", "gpu_launches", "clocks"} <= set(d)
+    r = d["roofline"]
+    assert {"bound", "achieved", "peak", "unit", "frac", "traffic"} <= set(r)
+    assert r["bound"] == "hbm" and 0 < r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert d["gpu_launches"] > 0 and d["value"] > 0 and d["n_gpus"] == 1
+    e = d["e2e"]
+    assert e["value"] > 0 and e["h2d_bytes_per_step"] == 32 * 64 ** 3 and e["d2h_bytes_per_step"] == 8
+    assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
