@@ -323,6 +323,16 @@ class Box:
     def clear_error(self):
         self._check(self._lib.fish_clear_error(self.ctx), "fish_clear_error")
 
+    def sync_quiet(self):
+        """Wait for the queued work; a non-physical status it reported is
+        returned (True) and cleared instead of raised.  Other errors raise."""
+        code = self._lib.fish_sync(self.ctx)
+        if code == FISH_ERR_NONPHYSICAL:
+            self.clear_error()
+            return True
+        self._check(code, "fish_sync")
+        return False
+
     def launch_count(self):
         return int(self._lib.fish_launch_count(self.ctx))
 

@@ -14,7 +14,8 @@ BASE_KEYS = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_ste
 
 def run_bench(*args, timeout=900):
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], cwd=ROOT, capture_output=True,
-                         text=True, timeout=timeout, check=True)
+                         text=True, timeout=timeout)
+    assert out.returncode == 0, out.stderr[-3000:]
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1, out.stdout
     return json.loads(lines[0])
@@ -30,12 +31,14 @@ def test_reference_arm_line():
 
 @pytest.mark.gpu
 def test_gpu_arm_line():
-    d = run_bench("--n", "64", "--steps", "3", "--warmup", "3", "--no-batch", "--no-fp64", "--no-cpu-baseline")
+    # 128^3: the coarser twins of the turbulence box reach p < 0 within the
+    # steps this run takes (warm-up, timed step, per-operator timing, e2e)
+    d = run_bench("--n", "128", "--steps", "1", "--warmup", "3", "--no-batch", "--no-fp64", "--no-cpu-baseline")
     assert BASE_KEYS <= set(d) and {"roofline", "gpu_launches", "clocks"} <= set(d)
     r = d["roofline"]
     assert {"bound", "achieved", "peak", "unit", "frac", "traffic"} <= set(r)
     assert r["bound"] == "hbm" and 0 < r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert d["gpu_launches"] > 0 and d["value"] > 0 and d["n_gpus"] == 1
     e = d["e2e"]
-    assert e["value"] > 0 and e["h2d_bytes_per_step"] == 32 * 64 ** 3 and e["d2h_bytes_per_step"] == 8
+    assert e["value"] > 0 and e["h2d_bytes_per_step"] == 32 * 128 ** 3 and e["d2h_bytes_per_step"] == 8
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
