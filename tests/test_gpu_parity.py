@@ -546,3 +546,33 @@ def test_fp64_fma_probe(F):
     FMA rate bound (152 SMs x 128 lanes x 2.1 GHz)."""
     r = F.probe_fp64_fma()
     assert 1e9 < r < 152 * 128 * 2.1e9
+
+
+def test_turbulence_twin_128():
+    """The 128^3 twin of the throughput workload (seeded random-phase MHD
+    turbulence): FP64 GPU path 1e-12 per cell and FP32 path L1(rho) 1e-5
+    against the oracle after four double steps (the twin stays physical for
+    about ten)."""
+    import paper_0910_2854_gb300 as F
+    from paper_0910_2854_gb300 import build
+    build.build()
+    F.load()
+    w = W.turbulence(128)
+    ob = oracle.OracleBox(*w.dims, w.gamma, bc=w.bc, h=w.h)
+    ob.set_state(w.state)
+    boxes = {}
+    for prec in ("fp64", "fp32"):
+        boxes[prec] = F.Box(*w.dims, w.gamma, bc=w.bc, precision=prec, h=w.h)
+        boxes[prec].set_state(w.state)
+    for _ in range(4):
+        dt = ob.cfl(0.5)
+        ob.step(dt)
+        for b in boxes.values():
+            b.step(dt)
+    assert ob.flags == 0
+    assert rel_err(boxes["fp64"].get_state(), ob.state) <= 1e-12
+    st = boxes["fp32"].get_state()
+    l1 = np.mean(np.abs(st[0] - ob.state[0])) / np.mean(np.abs(ob.state[0]))
+    assert l1 <= 1e-5, l1
+    for b in boxes.values():
+        b.close()
