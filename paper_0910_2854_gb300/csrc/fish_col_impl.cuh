@@ -47,6 +47,7 @@ static cudaError_t col_fluid_lim(const ColFluidArgs<typename VT<V>::S> &A, cudaS
         if (A.wd) return cudaErrorInvalidValue;
         if (A.lim == LIM_VANLEER) return col_fluid_launch<V, HSE, GRAV, LIM_VANLEER, FT1>(A, s);
         if (A.lim == LIM_MINMOD) return col_fluid_launch<V, HSE, GRAV, LIM_MINMOD, FT1>(A, s);
+        if (A.lim == LIM_HYBRID) return col_fluid_launch<V, HSE, GRAV, LIM_HYBRID, FT1>(A, s);
         return cudaErrorInvalidValue;
     } else {
         // irregular mesh: widths along d (limiter read at run time)

@@ -280,6 +280,10 @@ __device__ __forceinline__ void cflux2(const CCell<V> &c0, const CCell<V> &c1, c
         if (lim == LIM_HYBRID)
             lim = (vabs(c1.vn) > c1.cs || vabs(c2.vn) > c2.cs) ? LIM_MINMOD : LIM_VANLEER;
     }
+    // compile-time hybrid (LIM = LIM_HYBRID, packed kernels): per lane,
+    // sup > 0 where either cell is supersonic (|v| - c_S > 0 iff |v| > c_S)
+    V sup = vb<V>(0.0f);
+    if constexpr (LIM == LIM_HYBRID) sup = vmax(vabs(c1.vn) - c1.cs, vabs(c2.vn) - c2.cs);
     if constexpr (!HSE && !VT<V>::F64) {
         // FP32: F = (F_e + F_{e+1})/2 - D du_e/2 + [phi(+) - phi(-)]/4 with the
         // split-flux slopes written as dF +- D du (each one multiply-add)
@@ -294,6 +298,11 @@ __device__ __forceinline__ void cflux2(const CCell<V> &c0, const CCell<V> &c1, c
             if constexpr (NU) {
                 slp = w1 * vlimit<LIM>(vdiv(vfma(D, du0, df0), gl), vdiv(vfma(D, du1, df1), gc), lim);
                 slm = w2 * vlimit<LIM>(vdiv(vfma(nD, du1, df1), gc), vdiv(vfma(nD, du2, df2), gr), lim);
+            } else if constexpr (LIM == LIM_HYBRID) {
+                const V ap = vfma(D, du0, df0), bp = vfma(D, du1, df1);
+                const V am = vfma(nD, du1, df1), bm = vfma(nD, du2, df2);
+                slp = vsel_pos(sup, vminmod(ap, bp), vvanleer(ap, bp));
+                slm = vsel_pos(sup, vminmod(am, bm), vvanleer(am, bm));
             } else {
                 slp = vlimit<LIM>(vfma(D, du0, df0), vfma(D, du1, df1), lim);
                 slm = vlimit<LIM>(vfma(nD, du1, df1), vfma(nD, du2, df2), lim);

@@ -42,13 +42,13 @@ static inline bool frame_of(const Geom &g, int d, Frame &F)
 }
 
 // The two-column FP32 kernels are used for even fast extents without the
-// hydrostatic correction and with the Van Leer or minmod limiter.
+// hydrostatic correction and with the Van Leer, minmod or hybrid limiter.
 template <class T> static bool uses_pairs(const Frame &F, int lim, bool hse)
 {
 #ifdef FISH_FLUID_SCALAR
     return false;
 #else
-    return sizeof(T) == 4 && F.nf % 2 == 0 && !hse && (lim == LIM_VANLEER || lim == LIM_MINMOD);
+    return sizeof(T) == 4 && F.nf % 2 == 0 && !hse && (lim == LIM_VANLEER || lim == LIM_MINMOD || lim == LIM_HYBRID);
 #endif
 }
 

@@ -11,6 +11,10 @@ on one GPU and printed as one JSON line each:
       and both throughputs.
   python -m paper_0910_2854_gb300.reports batch
       the seeded batch of 64 uneven boxes: autotuned choice and throughput.
+  python -m paper_0910_2854_gb300.reports variants [n] [steps]
+      the FP32 turbulence box n^3 advanced with each variant of the method
+      (Van Leer, hybrid limiter, irregular mesh, unsplit and split gravity
+      in a smooth potential): ms per double step and cell-updates/s.
   python -m paper_0910_2854_gb300.reports fp64_sweeps [n]
       the FP64 path on the Orszag-Tang box n^3: one double step and each
       operator timed with CUDA events, next to the probed FP64 FMA rate of
@@ -129,6 +133,42 @@ def fp64_sweeps(n=128, steps=3, k=0.5):
     box.sync()
     box.close()
     out["fp64_fma_per_s"] = probe_fp64_fma()
+    return out
+
+
+def variants(n=512, steps=5, k=0.5):
+    import torch
+    from . import FISH_LIM_HYBRID
+    w = W.turbulence(n, device="cuda", dtype=torch.float32)
+    x = (np.arange(n) + 0.5) / n
+    widths = [(1.0 + 0.3 * np.sin(2 * np.pi * (x + 0.1 * a))) / n for a in range(3)]
+    widths = [wd / wd.sum() for wd in widths]
+    phi = None
+    out = {"report": "variants", "n": n, "steps": steps, "cfl": k, "precision": "fp32", "cases": {}}
+    cases = [("vanleer", {}), ("hybrid", {"limiter": FISH_LIM_HYBRID}), ("irregular_mesh", {"mesh": True}),
+             ("gravity_unsplit", {"grav": True}), ("gravity_split", {"grav": True, "gravity": "split"})]
+    for name, opt in cases:
+        kw = {key: opt[key] for key in ("limiter", "gravity") if key in opt}
+        box = Box(n, n, n, w.gamma, precision="fp32", h=w.h, **kw)
+        if opt.get("mesh"):
+            box.set_mesh(widths)
+        box.set_state(w.state)
+        if opt.get("grav"):
+            if phi is None:
+                # a smooth periodic potential well, weak against the
+                # turbulent pressure (|grad phi| ~ 0.5)
+                zz = np.cos(2 * np.pi * x)[:, None, None]
+                yy = np.cos(2 * np.pi * x)[None, :, None]
+                xx = np.cos(2 * np.pi * x)[None, None, :]
+                phi = -0.08 * (xx + yy + zz)
+                phi = np.broadcast_to(phi, (n, n, n)).copy()
+            box.set_potential(phi)
+        box.step_cfl(k, 1)
+        box.sync()
+        ms = _timed_steps(box, torch, k, steps) / steps
+        out["cases"][name] = {"ms_per_step": ms, "cell_updates_per_s": n ** 3 / (ms * 1e-3)}
+        box.close()
+        torch.cuda.empty_cache()
     return out
 
 
@@ -283,7 +323,7 @@ def main(argv):
         return
     args = [int(a) for a in argv[2:]]
     res = {"polytrope": polytrope, "fp32_vs_fp64": fp32_vs_fp64, "batch": batch,
-           "fp64_sweeps": fp64_sweeps}[what](*args)
+           "fp64_sweeps": fp64_sweeps, "variants": variants}[what](*args)
     res["wall_s"] = time.time() - t0
     print(json.dumps(res), flush=True)
 
