@@ -128,8 +128,8 @@ int fish_set_potential(fish_ctx *ctx, const double *phi);
  * the centre distances, potential differences are taken over the centre
  * span, CT face and edge velocities are linear interpolations, the CFL step
  * follows eq0420 and fish_diagnostics weights each cell by its own volume.
- * Ghost cells have the width of the cell they copy.  The one-column kernels
- * run every sweep (no packed FP32x2 path, no CFL fused into the last sweep).
+ * Ghost cells have the width of the cell they copy.  No CFL is fused into
+ * the last sweep (a separate CFL pass reads the widths).
  * Widths are uploaded at the next stepping call.  FISH_ERR_ARG on a bad
  * width. */
 int fish_set_mesh(fish_ctx *ctx, const double *dx, const double *dy, const double *dz);

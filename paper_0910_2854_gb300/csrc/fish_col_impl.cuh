@@ -43,8 +43,13 @@ template <class V, bool HSE, bool GRAV, bool FT1>
 static cudaError_t col_fluid_lim(const ColFluidArgs<typename VT<V>::S> &A, cudaStream_t s)
 {
     if constexpr (std::is_same<V, P2>::value) {
-        // compile-time limiters for the throughput path (uniform meshes only)
-        if (A.wd) return cudaErrorInvalidValue;
+        // compile-time limiters for the throughput path
+        if (A.wd) {
+            if (A.lim == LIM_VANLEER) return col_fluid_launch<V, HSE, GRAV, LIM_VANLEER, FT1, true>(A, s);
+            if (A.lim == LIM_MINMOD) return col_fluid_launch<V, HSE, GRAV, LIM_MINMOD, FT1, true>(A, s);
+            if (A.lim == LIM_HYBRID) return col_fluid_launch<V, HSE, GRAV, LIM_HYBRID, FT1, true>(A, s);
+            return cudaErrorInvalidValue;
+        }
         if (A.lim == LIM_VANLEER) return col_fluid_launch<V, HSE, GRAV, LIM_VANLEER, FT1>(A, s);
         if (A.lim == LIM_MINMOD) return col_fluid_launch<V, HSE, GRAV, LIM_MINMOD, FT1>(A, s);
         if (A.lim == LIM_HYBRID) return col_fluid_launch<V, HSE, GRAV, LIM_HYBRID, FT1>(A, s);

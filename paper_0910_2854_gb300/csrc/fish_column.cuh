@@ -395,7 +395,7 @@ template <class V> struct FRaw {
     V bo, bom; // other-axis transverse face field at own / lower face
     V phi;
     typename VT<V>::S bfm;  // fast-axis field at the face below the first column
-    V w;       // cell width along d (irregular mesh)
+    typename VT<V>::S w;    // cell width along d (irregular mesh; the same for all columns of a group)
 };
 
 template <class V> struct FMarch {
@@ -410,7 +410,7 @@ template <class V> struct FMarch {
     V phm2;              // potential of raw cell r-2
     Checks<V> chk;
     V cflr;              // largest CFL rate of the output cells (CFLF)
-    V w0, w1, w2, w3, w4;  // irregular mesh: widths of raw cells r, r-1, .. r-4
+    typename VT<V>::S w0, w1, w2, w3, w4;  // irregular mesh: widths of raw cells r, r-1, .. r-4
 };
 
 template <class S> struct FCtx {
@@ -446,8 +446,7 @@ __device__ __forceinline__ void fload_mapped(const ColFluidArgs<typename VT<V>::
             if (A.bc == BC_OUTFLOW && (s < 0 || s >= A.n)) R.phi = vb<V>(0.0f);
     }
     // a ghost has the width of the cell it copies (reading C-23)
-    if constexpr (VT<V>::W == 1)
-        if (A.wd) R.w = A.wd[cc];
+    if (A.wd) R.w = A.wd[cc];
 }
 
 // load interior cell at element offset i (no map; its lower b_d face is the
@@ -569,7 +568,7 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
         V lh = lamh;
         if constexpr (NU) {
             if constexpr (VT<V>::F64) lh = dt / (2.0 * M.w1);
-            else lh = vdiv(hdt, M.w1);
+            else lh = vdiv(hdt, vb<V>(M.w1));
         }
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
@@ -581,7 +580,7 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
             // centre span, reading C-26)
             V dphi;
             if constexpr (NU) {
-                const V span = vb<V>(0.5f) * M.w2 + M.w1 + vb<V>(0.5f) * M.w0;
+                const V span = vb<V>(0.5f) * vb<V>(M.w2) + vb<V>(M.w1) + vb<V>(0.5f) * vb<V>(M.w0);
                 if constexpr (VT<V>::F64) dphi = (phr - M.phm2) / span;
                 else dphi = vdiv(M.ph[p2] + M.phm2, span);
             } else if constexpr (VT<V>::F64) {
@@ -599,12 +598,12 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
             // corrector flux at (r-3, r-2) from predicted cells r-4 .. r-1 (eq0230)
             constexpr int s0 = K & 3, s1 = (K + 1) & 3, s2 = (K + 2) & 3;
             cflux2<V, HSE, LIM, NU>(M.P[s0], M.P[s1], M.P[s2], M.P[s3], M.q[s0], M.q[s1], M.q[s2], M.q[s3],
-                                    M.F2[k2], A.lim, M.w4, M.w3, M.w2, M.w1);
+                                    M.F2[k2], A.lim, vb<V>(M.w4), vb<V>(M.w3), vb<V>(M.w2), vb<V>(M.w1));
             if constexpr ((ST & ST_OUT) != 0) {
                 V lo = lam;
                 if constexpr (NU) {
                     if constexpr (VT<V>::F64) lo = dt / M.w3;
-                    else lo = vdiv(dt, M.w3);
+                    else lo = vdiv(dt, vb<V>(M.w3));
                 }
 #pragma unroll
                 for (int k = 0; k < 5; ++k) {
@@ -615,7 +614,7 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
                     // corrector source from the predicted state (eq0255)
                     V dphi;
                     if constexpr (NU) {
-                        const V span = vb<V>(0.5f) * M.w4 + M.w3 + vb<V>(0.5f) * M.w2;
+                        const V span = vb<V>(0.5f) * vb<V>(M.w4) + vb<V>(M.w3) + vb<V>(0.5f) * vb<V>(M.w2);
                         if constexpr (VT<V>::F64) dphi = (M.q[s2] - M.q[s0]) / span;
                         else dphi = vdiv(M.q[s0] + M.q[s1], span);
                     } else if constexpr (VT<V>::F64) {
@@ -704,7 +703,7 @@ __device__ __forceinline__ void fluid_columns(const ColFluidArgs<typename VT<V>:
     M.cflr = vb<V>(0.0f);
     M.phm2 = vb<V>(0.0f);
     M.ph[0] = M.ph[1] = vb<V>(0.0f);
-    M.w0 = M.w1 = M.w2 = M.w3 = M.w4 = vb<V>(1.0f);
+    M.w0 = M.w1 = M.w2 = M.w3 = M.w4 = typename VT<V>::S(1);
     fload_mapped<V, GRAV, FT1>(A, X, -3, M.R);
     constexpr int ALL = ST_F1 | ST_PRED | ST_F2 | ST_OUT;
     int r = 3;

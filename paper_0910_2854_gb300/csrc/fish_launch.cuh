@@ -107,8 +107,7 @@ cudaError_t Launch<T>::fluid(const T *const in[8], T *const out[5], const T *phi
         return col_fluid<double>(A, hse, F.ft1, s);
     } else {
         // two columns per thread (packed FP32x2) when the fast extent is even
-        // (uniform meshes)
-        if (!w3 && uses_pairs<T>(F, lim, hse)) return col_fluid<P2>(A, hse, true, s);
+        if (uses_pairs<T>(F, lim, hse)) return col_fluid<P2>(A, hse, true, s);
         return col_fluid<float>(A, hse, true, s);
     }
 }
