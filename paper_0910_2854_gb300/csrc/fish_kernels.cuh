@@ -303,47 +303,64 @@ template <class T> struct GravArgs {
     const T *phi;
     const double *dt;
     double frac;
-    long long N, sd;
-    int n, bc;
+    Geom g;                 // layout; d is not its fastest axis
+    int d;
     double h;
     const T *wd = nullptr;  // irregular mesh: cell widths along d (centre span, reading C-26)
 };
 
+// One block per row of the fastest memory axis at a time (grid-stride over
+// rows): the coordinate along d, the neighbour offsets and the centre span
+// are constant along a row, so the per-cell work is the kick alone.
 template <class T>
 __global__ void __launch_bounds__(256) gravity_kernel(GravArgs<T> A)
 {
+    const Geom &g = A.g;
+    const int f0 = g.ord[0], f1 = g.ord[1], f2 = g.ord[2];
+    const int nf = g.n[f0], nm = g.n[f1];
+    const long long rows = (long long)nm * g.n[f2];
+    const int n = g.n[A.d];
     const double tau = A.frac * *A.dt;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < A.N;
-         i += (long long)gridDim.x * blockDim.x) {
-        const int s = (int)((i / A.sd) % A.n);
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int m = (int)(row % nm), k = (int)(row / nm);
+        const long long base = (long long)m * g.st[f1] + (long long)k * g.st[f2];
+        const int s = A.d == f1 ? m : k;
+        const long long sd = g.st[A.d];
+        const long long op = (long long)(gmap(s + 1, n, g.bc) - s) * sd;
+        const long long om = (long long)(gmap(s - 1, n, g.bc) - s) * sd;
         if constexpr (sizeof(T) == 8) {
-            const long long ip = i + (long long)(gmap(s + 1, A.n, A.bc) - s) * A.sd;
-            const long long im = i + (long long)(gmap(s - 1, A.n, A.bc) - s) * A.sd;
-            const double span = A.wd ? 0.5 * A.wd[gmap(s - 1, A.n, A.bc)] + A.wd[s] + 0.5 * A.wd[gmap(s + 1, A.n, A.bc)]
+            const double span = A.wd ? 0.5 * A.wd[gmap(s - 1, n, g.bc)] + A.wd[s] + 0.5 * A.wd[gmap(s + 1, n, g.bc)]
                                      : 2.0 * A.h;
-            const double dphi = (A.phi[ip] - A.phi[im]) / span;
-            const double rho = A.rho[i];
-            const double mo = A.md[i];
-            const double mn = mo - tau * rho * dphi;
-            A.md[i] = mn;
-            A.E[i] = A.E[i] + 0.5 * (mn * mn - mo * mo) / rho;
-        } else {
-            float dm1;
-            if (s > 0) dm1 = A.phi[i - A.sd];
-            else dm1 = A.bc == BC_PERIODIC ? A.phi[i + (long long)(A.n - 1) * A.sd] : 0.0f;
-            float dphi;
-            if (A.wd) {
-                const float span = 0.5f * (float)A.wd[gmap(s - 1, A.n, A.bc)] + (float)A.wd[s] +
-                                   0.5f * (float)A.wd[gmap(s + 1, A.n, A.bc)];
-                dphi = (A.phi[i] + dm1) / span;
-            } else {
-                dphi = (A.phi[i] + dm1) * (float)(0.5 / A.h);
+            for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+                const long long i = base + f;
+                const double dphi = (A.phi[i + op] - A.phi[i + om]) / span;
+                const double rho = A.rho[i];
+                const double mo = A.md[i];
+                const double mn = mo - tau * rho * dphi;
+                A.md[i] = mn;
+                A.E[i] = A.E[i] + 0.5 * (mn * mn - mo * mo) / rho;
             }
-            const float rho = A.rho[i];
-            const float mo = A.md[i];
-            const float dm = -((float)tau * rho) * dphi;
-            A.md[i] = mo + dm;
-            A.E[i] = A.E[i] + dm * (mo + 0.5f * dm) / rho;
+        } else {
+            // phi_{s+1} - phi_{s-1} = D_s + D_{s-1}; D_{-1} = 0 at an outflow boundary
+            const bool lower = s > 0 || g.bc == BC_PERIODIC;
+            float rspan;
+            if (A.wd) {
+                rspan = 1.0f / (0.5f * (float)A.wd[gmap(s - 1, n, g.bc)] + (float)A.wd[s] +
+                                0.5f * (float)A.wd[gmap(s + 1, n, g.bc)]);
+            } else {
+                rspan = (float)(0.5 / A.h);
+            }
+            const float ftau = (float)tau;
+            for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+                const long long i = base + f;
+                const float dm1 = lower ? A.phi[i + om] : 0.0f;
+                const float dphi = (A.phi[i] + dm1) * rspan;
+                const float rho = A.rho[i];
+                const float mo = A.md[i];
+                const float dm = -(ftau * rho) * dphi;
+                A.md[i] = mo + dm;
+                A.E[i] = A.E[i] + __fdividef(dm * (mo + 0.5f * dm), rho);
+            }
         }
     }
 }

@@ -218,7 +218,7 @@ template <class T>
 cudaError_t Launch<T>::gravity(T *const u[5], const T *phi, const double *dt, double frac, const Geom &g, int d,
                                double h, cudaStream_t s, const T *wd)
 {
-    if (!phi || d < 0 || d > 2) return cudaErrorInvalidValue;
+    if (!phi || d < 0 || d > 2 || g.ord[0] == d) return cudaErrorInvalidValue;
     GravArgs<T> A;
     A.rho = u[0];
     A.md = u[1 + d];
@@ -226,15 +226,13 @@ cudaError_t Launch<T>::gravity(T *const u[5], const T *phi, const double *dt, do
     A.phi = phi;
     A.dt = dt;
     A.frac = frac;
-    A.N = (long long)g.n[0] * g.n[1] * g.n[2];
-    A.sd = g.st[d];
-    A.n = g.n[d];
-    A.bc = g.bc;
+    A.g = g;
+    A.d = d;
     A.h = h;
     A.wd = wd;
-    unsigned gr = grid_for(A.N, 256);
-    if (gr > 152u * 16u) gr = 152u * 16u;
-    gravity_kernel<T><<<gr, 256, 0, s>>>(A);
+    const long long rows = (long long)g.n[g.ord[1]] * g.n[g.ord[2]];
+    const unsigned grid = (unsigned)(rows < 152ll * 8 ? rows : 152ll * 8);
+    gravity_kernel<T><<<grid, 256, 0, s>>>(A);
     return cudaGetLastError();
 }
 
