@@ -2,8 +2,10 @@
 
 Three translation units compiled in parallel, then linked:
   fish_f64.cu  -- FP64 kernels, -fmad=false (IEEE rounding of each operation)
+  fish_f64_t2.cu -- the FP64 sweeps with the fast axis t2, same flags
   fish_f32.cu  -- FP32 kernels (FMA contraction allowed)
-  fish_p2.cu   -- FP32 two-column sweep kernels (packed FP32x2)
+  fish_p2.cu   -- FP32 two-column sweep kernels (packed FP32x2), Van Leer
+  fish_p2_mm.cu, fish_p2_hy.cu -- the same with the minmod / hybrid limiter
   fish_capi.cu -- host-side C ABI
   fish_noalloc.cu -- the allocation-free diagnostics entry point
   fish_batch.cu -- batches of independent boxes (FP32)
@@ -24,8 +26,11 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
           "--expt-relaxed-constexpr", "-I", CSRC, "-I", os.path.join(os.path.dirname(HERE), "include")]
 UNITS = {
     "fish_f64.cu": ["-fmad=false"],
+    "fish_f64_t2.cu": ["-fmad=false"],
     "fish_f32.cu": ["-prec-sqrt=false", "-ftz=true"],
     "fish_p2.cu": ["-prec-sqrt=false", "-ftz=true"],
+    "fish_p2_mm.cu": ["-prec-sqrt=false", "-ftz=true"],
+    "fish_p2_hy.cu": ["-prec-sqrt=false", "-ftz=true"],
     "fish_capi.cu": [],
     "fish_noalloc.cu": [],
     "fish_batch.cu": ["-prec-sqrt=false", "-ftz=true"],

@@ -20,8 +20,10 @@ template <class V> static unsigned fluid_blocks(const ColFluidArgs<typename VT<V
     return col_grid((long long)(A.nf / VT<V>::W) * A.no, 128);
 }
 
+// (external linkage: the packed instantiations are spread over several
+// translation units that compile in parallel)
 template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool NU = false>
-static cudaError_t col_fluid_launch(const ColFluidArgs<typename VT<V>::S> &A, cudaStream_t s)
+cudaError_t col_fluid_launch(const ColFluidArgs<typename VT<V>::S> &A, cudaStream_t s)
 {
     if constexpr (NU) {
         if (A.cfl_min) return cudaErrorInvalidValue;
@@ -43,11 +45,10 @@ template <class V, bool HSE, bool GRAV, bool FT1>
 static cudaError_t col_fluid_lim(const ColFluidArgs<typename VT<V>::S> &A, cudaStream_t s)
 {
     if constexpr (std::is_same<V, P2>::value) {
-        // compile-time limiters for the throughput path
+        // compile-time limiters for the throughput path (an irregular mesh
+        // with Van Leer; its other limiters run on the one-column kernels)
         if (A.wd) {
             if (A.lim == LIM_VANLEER) return col_fluid_launch<V, HSE, GRAV, LIM_VANLEER, FT1, true>(A, s);
-            if (A.lim == LIM_MINMOD) return col_fluid_launch<V, HSE, GRAV, LIM_MINMOD, FT1, true>(A, s);
-            if (A.lim == LIM_HYBRID) return col_fluid_launch<V, HSE, GRAV, LIM_HYBRID, FT1, true>(A, s);
             return cudaErrorInvalidValue;
         }
         if (A.lim == LIM_VANLEER) return col_fluid_launch<V, HSE, GRAV, LIM_VANLEER, FT1>(A, s);
@@ -88,7 +89,7 @@ cudaError_t col_fluid(const ColFluidArgs<typename VT<V>::S> &A, bool hse, bool f
 }
 
 template <class V, int LIM, bool FT1, bool NU = false>
-static cudaError_t col_ct_launch(const ColCTArgs<typename VT<V>::S> &A, cudaStream_t s)
+cudaError_t col_ct_launch(const ColCTArgs<typename VT<V>::S> &A, cudaStream_t s)
 {
     // one warp per 31 W columns of a row (plus a halo lane); a block takes
     // one segment of FISH_CT_ROWS consecutive rows

@@ -5,6 +5,21 @@
 #include "fish_launch.cuh"
 
 namespace fish {
+// the sweeps whose fast axis is t2 (FT1 = false) compile in fish_f64_t2.cu
+#define FISH_F64_T2(HSE, GRAV, NU)                                                                                \
+    extern template cudaError_t col_fluid_launch<double, HSE, GRAV, -1, false, NU>(const ColFluidArgs<double> &,  \
+                                                                                   cudaStream_t);
+FISH_F64_T2(false, false, false)
+FISH_F64_T2(false, false, true)
+FISH_F64_T2(false, true, false)
+FISH_F64_T2(false, true, true)
+FISH_F64_T2(true, false, false)
+FISH_F64_T2(true, false, true)
+FISH_F64_T2(true, true, false)
+FISH_F64_T2(true, true, true)
+#undef FISH_F64_T2
+extern template cudaError_t col_ct_launch<double, -1, false, false>(const ColCTArgs<double> &, cudaStream_t);
+extern template cudaError_t col_ct_launch<double, -1, false, true>(const ColCTArgs<double> &, cudaStream_t);
 template struct Launch<double>;
 template cudaError_t col_fluid<double>(const ColFluidArgs<double> &, bool, bool, cudaStream_t);
 template cudaError_t col_ct<double>(const ColCTArgs<double> &, bool, cudaStream_t);

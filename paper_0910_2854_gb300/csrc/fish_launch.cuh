@@ -43,11 +43,12 @@ static inline bool frame_of(const Geom &g, int d, Frame &F)
 
 // The two-column FP32 kernels are used for even fast extents without the
 // hydrostatic correction and with the Van Leer, minmod or hybrid limiter.
-template <class T> static bool uses_pairs(const Frame &F, int lim, bool hse)
+template <class T> static bool uses_pairs(const Frame &F, int lim, bool hse, bool nu = false)
 {
 #ifdef FISH_FLUID_SCALAR
     return false;
 #else
+    if (nu && lim != LIM_VANLEER) return false;
     return sizeof(T) == 4 && F.nf % 2 == 0 && !hse && (lim == LIM_VANLEER || lim == LIM_MINMOD || lim == LIM_HYBRID);
 #endif
 }
@@ -107,7 +108,7 @@ cudaError_t Launch<T>::fluid(const T *const in[8], T *const out[5], const T *phi
         return col_fluid<double>(A, hse, F.ft1, s);
     } else {
         // two columns per thread (packed FP32x2) when the fast extent is even
-        if (uses_pairs<T>(F, lim, hse)) return col_fluid<P2>(A, hse, true, s);
+        if (uses_pairs<T>(F, lim, hse, w3 != nullptr)) return col_fluid<P2>(A, hse, true, s);
         return col_fluid<float>(A, hse, true, s);
     }
 }
