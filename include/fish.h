@@ -69,7 +69,9 @@ enum {
                                 (eq0253-eq0255); FISH_GRAV_SPLIT: L_d becomes G_d(dt/2) L_d G_d(dt/2)
                                 with G_d: m_d -= (dt/2) rho dphi/dx_d (centred difference) and E
                                 changed by the kinetic energy change (eq025111-eq02513).  Split
-                                gravity and FISH_OPT_HSE = 1 exclude each other (FISH_ERR_ARG). */
+                                gravity and FISH_OPT_HSE = 1 exclude each other (FISH_ERR_ARG).
+                                The kicks run inside the fluid sweep (separate passes on an
+                                irregular mesh). */
 };
 enum { FISH_GRAV_UNSPLIT = 0, FISH_GRAV_SPLIT = 1 };
 enum { FISH_PREC_FP64 = 0, FISH_PREC_FP32 = 1 };

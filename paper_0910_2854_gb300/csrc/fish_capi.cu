@@ -278,10 +278,13 @@ template <class T> int op_gravity(fish_ctx *c, int d)
 
 bool split_gravity(const fish_ctx *c) { return c->gsplit && c->has_phi; }
 
-// L_d, or G_d(dt/2) L_d G_d(dt/2) with operator-split gravity (eq025111)
+// L_d, or G_d(dt/2) L_d G_d(dt/2) with operator-split gravity (eq025111):
+// on a uniform mesh the kicks run inside the fluid march, on an irregular
+// one as separate passes around it
 template <class T> int op_fluid(fish_ctx *c, int d, bool fuse_cfl)
 {
-    const bool split = split_gravity(c);
+    const bool fused_split = split_gravity(c) && !c->nu;
+    const bool split = split_gravity(c) && !fused_split;
     int r;
     if (split && (r = op_gravity<T>(c, d))) return r;
     const T *in[8];
@@ -294,7 +297,7 @@ template <class T> int op_fluid(fish_ctx *c, int d, bool fuse_cfl)
     FISH_CK(c,
             Launch<T>::fluid(in, out, split ? nullptr : sweep_potential<T>(c, d), c->dt_dev,
                              geom(c), d, c->lim, c->hse != 0, c->gamma, c->alpha, c->h, c->flags,
-                             fuse_cfl ? c->minbits : nullptr, c->stream, mesh_of<T>(c).get()),
+                             fuse_cfl ? c->minbits : nullptr, c->stream, mesh_of<T>(c).get(), fused_split),
             "fluid sweep launch");
     c->cu = 1 - c->cu;
     c->launches += 1;
@@ -332,7 +335,7 @@ int apply_op(fish_ctx *c, int op, int d, bool fuse_cfl = false)
 // minimum of the new state (FP32 two-column kernels only).
 bool last_sweep_fuses_cfl(const fish_ctx *c)
 {
-    if (c->prec != FISH_PREC_FP32 || split_gravity(c) || c->nu) return false;
+    if (c->prec != FISH_PREC_FP32 || c->nu) return false;  // (split kicks run inside the march)
     return Launch<float>::fluid_fuses_cfl(geom_of(c, layout_for(0)), 0, c->lim, c->hse != 0);
 }
 

@@ -22,7 +22,7 @@ template <class V> static unsigned fluid_blocks(const ColFluidArgs<typename VT<V
 
 // (external linkage: the packed instantiations are spread over several
 // translation units that compile in parallel)
-template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool NU = false>
+template <class V, bool HSE, int GRAV, int LIM, bool FT1, bool NU = false>
 cudaError_t col_fluid_launch(const ColFluidArgs<typename VT<V>::S> &A, cudaStream_t s)
 {
     if constexpr (NU) {
@@ -41,15 +41,22 @@ cudaError_t col_fluid_launch(const ColFluidArgs<typename VT<V>::S> &A, cudaStrea
     return cudaGetLastError();
 }
 
-template <class V, bool HSE, bool GRAV, bool FT1>
+// GRAV: 0 no potential, 1 unsplit source terms, 2 split kicks in the march
+// (uniform meshes; with an irregular mesh the kicks run as separate passes)
+template <class V, bool HSE, int GRAV, bool FT1>
 static cudaError_t col_fluid_lim(const ColFluidArgs<typename VT<V>::S> &A, cudaStream_t s)
 {
+    if constexpr (GRAV == 2) {
+        if (A.wd) return cudaErrorInvalidValue;
+    }
     if constexpr (std::is_same<V, P2>::value) {
         // compile-time limiters for the throughput path (an irregular mesh
         // with Van Leer; its other limiters run on the one-column kernels)
-        if (A.wd) {
-            if (A.lim == LIM_VANLEER) return col_fluid_launch<V, HSE, GRAV, LIM_VANLEER, FT1, true>(A, s);
-            return cudaErrorInvalidValue;
+        if constexpr (GRAV != 2) {
+            if (A.wd) {
+                if (A.lim == LIM_VANLEER) return col_fluid_launch<V, HSE, GRAV, LIM_VANLEER, FT1, true>(A, s);
+                return cudaErrorInvalidValue;
+            }
         }
         if (A.lim == LIM_VANLEER) return col_fluid_launch<V, HSE, GRAV, LIM_VANLEER, FT1>(A, s);
         if (A.lim == LIM_MINMOD) return col_fluid_launch<V, HSE, GRAV, LIM_MINMOD, FT1>(A, s);
@@ -57,7 +64,9 @@ static cudaError_t col_fluid_lim(const ColFluidArgs<typename VT<V>::S> &A, cudaS
         return cudaErrorInvalidValue;
     } else {
         // irregular mesh: widths along d (limiter read at run time)
-        if (A.wd) return col_fluid_launch<V, HSE, GRAV, -1, FT1, true>(A, s);
+        if constexpr (GRAV != 2) {
+            if (A.wd) return col_fluid_launch<V, HSE, GRAV, -1, FT1, true>(A, s);
+        }
         return col_fluid_launch<V, HSE, GRAV, -1, FT1>(A, s);
     }
 }
@@ -67,13 +76,16 @@ static cudaError_t col_fluid_ft(const ColFluidArgs<typename VT<V>::S> &A, bool h
 {
     if constexpr (std::is_same<V, P2>::value) {
         if (hse) return cudaErrorInvalidValue;  // the packed kernels carry no hydrostatic terms
-        if (A.phi) return col_fluid_lim<V, false, true, FT1>(A, s);
-        return col_fluid_lim<V, false, false, FT1>(A, s);
+        if (A.phi && A.sg) return col_fluid_lim<V, false, 2, FT1>(A, s);
+        if (A.phi) return col_fluid_lim<V, false, 1, FT1>(A, s);
+        return col_fluid_lim<V, false, 0, FT1>(A, s);
     } else {
-        if (hse && A.phi) return col_fluid_lim<V, true, true, FT1>(A, s);
-        if (hse) return col_fluid_lim<V, true, false, FT1>(A, s);  // correction with phi = 0
-        if (A.phi) return col_fluid_lim<V, false, true, FT1>(A, s);
-        return col_fluid_lim<V, false, false, FT1>(A, s);
+        if (hse && A.sg) return cudaErrorInvalidValue;  // split gravity and the correction exclude each other
+        if (hse && A.phi) return col_fluid_lim<V, true, 1, FT1>(A, s);
+        if (hse) return col_fluid_lim<V, true, 0, FT1>(A, s);  // correction with phi = 0
+        if (A.phi && A.sg) return col_fluid_lim<V, false, 2, FT1>(A, s);
+        if (A.phi) return col_fluid_lim<V, false, 1, FT1>(A, s);
+        return col_fluid_lim<V, false, 0, FT1>(A, s);
     }
 }
 

@@ -50,6 +50,7 @@ template <class S> struct ColFluidArgs {
     unsigned long long *cfl_min;
     S rh[3];
     const S *wd = nullptr;  // irregular mesh (kernels built with NU): the n cell widths along d
+    int sg = 0;             // 1: phi drives operator-split kicks G_d(dt/2) around the sweep, not source terms
 };
 
 template <class S> struct ColCTArgs {
@@ -411,6 +412,7 @@ template <class V> struct FMarch {
     Checks<V> chk;
     V cflr;              // largest CFL rate of the output cells (CFLF)
     typename VT<V>::S w0, w1, w2, w3, w4;  // irregular mesh: widths of raw cells r, r-1, .. r-4
+    V dprev;             // split gravity: potential (FP64) or its difference (FP32) of raw cell r-1
 };
 
 template <class S> struct FCtx {
@@ -503,10 +505,53 @@ enum : int { LD_NONE = 0, LD_DIRECT = 1, LD_MAPPED = 2, LD_DIRECT_PF = 3 };
 // cell r+1 (kind LD) into M.R.  FT1: the fast axis is t1 (else t2).  NU:
 // irregular mesh along d (eq037): the cells' own widths replace h (the
 // widths of raw cells r .. r-4 ride along in M.w0 .. M.w4).
-template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool CFLF, bool NU, int K, int ST, int LD>
+// Operator-split gravity kick G_d(tau) of one cell (eq02512, reading C-22):
+// m_d -= tau rho dphi, E changes by the kinetic energy change; FP64 in the
+// oracle's operation order.
+template <class V> __device__ __forceinline__ void sg_kick(V u[5], V dk, V tau)
+{
+    if constexpr (VT<V>::F64) {
+        const V mo = u[1];
+        const V mn = mo - tau * u[0] * dk;
+        u[1] = mn;
+        u[4] = u[4] + 0.5 * (mn * mn - mo * mo) / u[0];
+    } else {
+        const V mo = u[1];
+        const V dm = -(tau * u[0]) * dk;
+        u[1] = mo + dm;
+        u[4] = u[4] + vdiv(dm * vfma(vb<V>(0.5f), dm, mo), u[0]);
+    }
+}
+
+// Centred potential difference (eq02513) of the image cell of ghost r (its
+// copy along d): FP64 from the potential, FP32 from the stored differences
+// D_c = phi_{c+1} - phi_c (D_{-1} = 0 at an outflow boundary).
+template <class V>
+__device__ __forceinline__ V sg_image_dk(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S> &X,
+                                         int r, V rtwoh)
+{
+    const int cc = gmap(r, A.n, A.bc);
+    if constexpr (VT<V>::F64) {
+        const V pp = vload<V>(A.phi, X.base + (long long)gmap(cc + 1, A.n, A.bc) * A.sd);
+        const V pm = vload<V>(A.phi, X.base + (long long)gmap(cc - 1, A.n, A.bc) * A.sd);
+        return (pp - pm) / (2.0 * A.h);
+    } else {
+        const V dc = vload<V>(A.phi, X.base + (long long)cc * A.sd);
+        V dl = vb<V>(0.0f);
+        if (cc > 0 || A.bc == BC_PERIODIC) dl = vload<V>(A.phi, X.base + (long long)gmap(cc - 1, A.n, A.bc) * A.sd);
+        return (dc + dl) * rtwoh;
+    }
+}
+
+// GM: gravity mode, 0 none, 1 unsplit source terms (eq0253-eq0255), 2
+// operator-split kicks G_d(dt/2) folded into the march (eq025111): the raw
+// cell is kicked as it is consumed, the output cell's old state before its
+// update and the result after it (reading C-22 for the kick).
+template <class V, bool HSE, int GM, int LIM, bool FT1, bool CFLF, bool NU, int K, int ST, int LD>
 __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S> &X,
                                       FMarch<V> &M, int r, V lam, V lamh, V hdt, V dt, V rtwoh)
 {
+    constexpr bool GRAV = GM == 1, SG = GM == 2, PHI = GM != 0;
     constexpr int k2 = K & 1, p2 = (K + 1) & 1;
     const V half = vb<V>(0.5f);
     // consume the raw input of cell r
@@ -525,7 +570,7 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
         bbr[1] = boc;
         bbr[2] = bfc;
     }
-    const V phr = GRAV ? M.R.phi : vb<V>(0.0f);  // no potential: phi = 0
+    const V phr = PHI ? M.R.phi : vb<V>(0.0f);  // no potential: phi = 0
     if constexpr (NU) {
         M.w4 = M.w3;
         M.w3 = M.w2;
@@ -535,15 +580,15 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
     }
     // prefetch raw cell r+1
     if constexpr (LD == LD_DIRECT || LD == LD_DIRECT_PF) {
-        fload_direct<V, GRAV, FT1>(A, X, X.base + (long long)(r + 1) * A.sd, M.R);
+        fload_direct<V, PHI, FT1>(A, X, X.base + (long long)(r + 1) * A.sd, M.R);
         if constexpr (NU) M.R.w = A.wd[r + 1];
         M.R.bdm = bd_r;
         if constexpr (LD == LD_DIRECT_PF) {
             const int pf = min(r + 1 + FISH_PF_DIST, A.n - 1);
-            fprefetch<V, GRAV, FT1>(A, X, X.base + (long long)pf * A.sd);
+            fprefetch<V, PHI, FT1>(A, X, X.base + (long long)pf * A.sd);
         }
     } else if constexpr (LD == LD_MAPPED) {
-        fload_mapped<V, GRAV, FT1>(A, X, r + 1, M.R);
+        fload_mapped<V, PHI, FT1>(A, X, r + 1, M.R);
     }
     // old state of the output cell o = r-3
     const int o = r - 3;
@@ -553,10 +598,26 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
 #pragma unroll
         for (int k = 0; k < 5; ++k) un[k] = vload<V>(A.u[k], io);
     }
+    if constexpr (SG) {
+        // kick of raw cell r with its centred potential difference (a ghost
+        // takes its image cell's), and of the output cell's old state
+        V dk;
+        if (r < 0 || r >= A.n) {
+            dk = sg_image_dk<V>(A, X, r, rtwoh);
+        } else if constexpr (VT<V>::F64) {
+            dk = (M.R.phi - M.dprev) / (2.0 * A.h);  // phi_{r+1} - phi_{r-1}
+        } else {
+            dk = (phr + M.dprev) * rtwoh;            // D_r + D_{r-1}
+        }
+        M.dprev = phr;
+        sg_kick<V>(ur, dk, hdt);
+        M.ph[k2] = dk;
+        if constexpr ((ST & ST_OUT) != 0) sg_kick<V>(un, M.q[(K + 1) & 3], hdt);
+    }
     ceval<V>(ur, bbr, vb<V>(A.gamma), vb<V>(A.gm1), M.C[k2], M.chk);
 #pragma unroll
     for (int k = 0; k < 3; ++k) M.bb[k2][k] = bbr[k];
-    if (GRAV || HSE) M.ph[k2] = phr;
+    if (!SG && (GRAV || HSE)) M.ph[k2] = phr;
     if constexpr ((ST & ST_F1) != 0) {
         // predictor flux at (r-1, r) (eq0140 / eq0324)
         cflux1<V, HSE>(M.C[p2], M.C[k2], M.ph[p2], phr, vb<V>(A.alpha), M.F1[k2]);
@@ -593,7 +654,7 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
         }
         constexpr int s3 = (K + 3) & 3;  // slot of cell r-1
         ceval<V>(up, M.bb[p2], vb<V>(A.gamma), vb<V>(A.gm1), M.P[s3], M.chk);
-        if (GRAV || HSE) M.q[s3] = M.ph[p2];
+        if (PHI || HSE) M.q[s3] = M.ph[p2];
         if constexpr ((ST & ST_F2) != 0) {
             // corrector flux at (r-3, r-2) from predicted cells r-4 .. r-1 (eq0230)
             constexpr int s0 = K & 3, s1 = (K + 1) & 3, s2 = (K + 2) & 3;
@@ -625,6 +686,7 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
                     un[1] = un[1] - dt * M.P[s1].u[0] * dphi;
                     un[4] = un[4] - dt * M.P[s1].u[1] * dphi;
                 }
+                if constexpr (SG) sg_kick<V>(un, M.q[s1], hdt);  // output cell: second half kick
 #pragma unroll
                 for (int k = 0; k < 5; ++k) vstore(A.uo[k], io, un[k]);
                 if constexpr (CFLF) {
@@ -657,7 +719,7 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
 
 // L_d over all columns.  The prologue runs raw cells -3 .. 2 (K = 1, 2, 3,
 // 0, 1, 2); boxes with n < 8 load everything through the map.
-template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool CFLF, bool NU, int PLD>
+template <class V, bool HSE, int GRAV, int LIM, bool FT1, bool CFLF, bool NU, int PLD>
 __device__ __forceinline__ void fprologue(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S> &X,
                                           FMarch<V> &M, V lam, V lamh, V hdt, V dt, V rtwoh)
 {
@@ -677,7 +739,7 @@ __device__ __forceinline__ void fprologue(const ColFluidArgs<typename VT<V>::S> 
 #endif
 
 // The march of thread cid (column group cid of the box described by A).
-template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool CFLF, bool NU = false>
+template <class V, bool HSE, int GRAV, int LIM, bool FT1, bool CFLF, bool NU = false>
 __device__ __forceinline__ void fluid_columns(const ColFluidArgs<typename VT<V>::S> &A, long long cid)
 {
     using S = typename VT<V>::S;
@@ -704,7 +766,8 @@ __device__ __forceinline__ void fluid_columns(const ColFluidArgs<typename VT<V>:
     M.phm2 = vb<V>(0.0f);
     M.ph[0] = M.ph[1] = vb<V>(0.0f);
     M.w0 = M.w1 = M.w2 = M.w3 = M.w4 = typename VT<V>::S(1);
-    fload_mapped<V, GRAV, FT1>(A, X, -3, M.R);
+    M.dprev = vb<V>(0.0f);
+    fload_mapped<V, GRAV != 0, FT1>(A, X, -3, M.R);
     constexpr int ALL = ST_F1 | ST_PRED | ST_F2 | ST_OUT;
     int r = 3;
     if (n >= 8) {
@@ -750,7 +813,7 @@ __device__ __forceinline__ void fluid_columns(const ColFluidArgs<typename VT<V>:
     }
 }
 
-template <class V, bool HSE, bool GRAV, int LIM, bool FT1, bool CFLF = false, bool NU = false>
+template <class V, bool HSE, int GRAV, int LIM, bool FT1, bool CFLF = false, bool NU = false>
 __global__ void __launch_bounds__(128, VT<V>::F64 ? 1 : (VT<V>::W == 2 || HSE ? FISH_COL_MINB : FISH_COL_MINB1))
     fluid_col_kernel(const ColFluidArgs<typename VT<V>::S> A)
 {

@@ -6,14 +6,15 @@
 namespace fish {
 #define FISH_F64_T2(HSE, GRAV, NU) \
     template cudaError_t col_fluid_launch<double, HSE, GRAV, -1, false, NU>(const ColFluidArgs<double> &, cudaStream_t);
-FISH_F64_T2(false, false, false)
-FISH_F64_T2(false, false, true)
-FISH_F64_T2(false, true, false)
-FISH_F64_T2(false, true, true)
-FISH_F64_T2(true, false, false)
-FISH_F64_T2(true, false, true)
-FISH_F64_T2(true, true, false)
-FISH_F64_T2(true, true, true)
+FISH_F64_T2(false, 0, false)
+FISH_F64_T2(false, 0, true)
+FISH_F64_T2(false, 1, false)
+FISH_F64_T2(false, 1, true)
+FISH_F64_T2(true, 0, false)
+FISH_F64_T2(true, 0, true)
+FISH_F64_T2(true, 1, false)
+FISH_F64_T2(true, 1, true)
+FISH_F64_T2(false, 2, false)
 #undef FISH_F64_T2
 template cudaError_t col_ct_launch<double, -1, false, false>(const ColCTArgs<double> &, cudaStream_t);
 template cudaError_t col_ct_launch<double, -1, false, true>(const ColCTArgs<double> &, cudaStream_t);

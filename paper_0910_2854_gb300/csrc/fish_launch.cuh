@@ -63,8 +63,11 @@ template <class T>
 cudaError_t Launch<T>::fluid(const T *const in[8], T *const out[5], const T *phi, const double *dt,
                              const Geom &g, int d, int lim, bool hse, double gamma, double alpha,
                              const double h3[3], unsigned *flags, unsigned long long *cfl_min, cudaStream_t s,
-                             const T *const *w3)
+                             const T *const *w3, bool split_gravity)
 {
+    // split gravity: phi drives kicks G_d(dt/2) folded into the march
+    // (uniform meshes with a potential, no hydrostatic correction)
+    if (split_gravity && (!phi || w3 || hse)) return cudaErrorInvalidValue;
     Frame F;
     if (!frame_of(g, d, F)) return cudaErrorInvalidValue;
     if (w3 && (!w3[0] || !w3[1] || !w3[2])) return cudaErrorInvalidValue;
@@ -104,6 +107,7 @@ cudaError_t Launch<T>::fluid(const T *const in[8], T *const out[5], const T *phi
     A.rh[1] = T(1.0 / h3[a1]);
     A.rh[2] = T(1.0 / h3[a2]);
     A.wd = w3 ? w3[d] : nullptr;
+    A.sg = split_gravity ? 1 : 0;
     if constexpr (sizeof(T) == 8) {
         return col_fluid<double>(A, hse, F.ft1, s);
     } else {

@@ -18,7 +18,7 @@ template <class T> struct Launch {
     static cudaError_t fluid(const T *const in[8], T *const out[5], const T *phi, const double *dt,
                              const Geom &g, int d, int lim, bool hse, double gamma, double alpha,
                              const double h3[3], unsigned *flags, unsigned long long *cfl_min, cudaStream_t s,
-                             const T *const *w3 = nullptr);
+                             const T *const *w3 = nullptr, bool split_gravity = false);
     static bool fluid_fuses_cfl(const Geom &g, int d, int lim, bool hse);
     // B_d: rho, m_d of the current state; b[3] current field, bout[3] other.
     static cudaError_t ct(const T *rho, const T *md, const T *const b[3], T *const bout[3],

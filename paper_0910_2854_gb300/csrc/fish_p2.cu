@@ -7,10 +7,12 @@
 
 namespace fish {
 #define FISH_P2_OTHER(LIMV)                                                                                     \
-    extern template cudaError_t col_fluid_launch<P2, false, false, LIMV, true, false>(const ColFluidArgs<float> &, \
-                                                                                     cudaStream_t);            \
-    extern template cudaError_t col_fluid_launch<P2, false, true, LIMV, true, false>(const ColFluidArgs<float> &,  \
-                                                                                    cudaStream_t);
+    extern template cudaError_t col_fluid_launch<P2, false, 0, LIMV, true, false>(const ColFluidArgs<float> &,  \
+                                                                                 cudaStream_t);                \
+    extern template cudaError_t col_fluid_launch<P2, false, 1, LIMV, true, false>(const ColFluidArgs<float> &,  \
+                                                                                 cudaStream_t);                \
+    extern template cudaError_t col_fluid_launch<P2, false, 2, LIMV, true, false>(const ColFluidArgs<float> &,  \
+                                                                                 cudaStream_t);
 FISH_P2_OTHER(LIM_MINMOD)
 FISH_P2_OTHER(LIM_HYBRID)
 #undef FISH_P2_OTHER

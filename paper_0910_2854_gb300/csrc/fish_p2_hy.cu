@@ -2,6 +2,7 @@
 #include "fish_col_impl.cuh"
 
 namespace fish {
-template cudaError_t col_fluid_launch<P2, false, false, LIM_HYBRID, true, false>(const ColFluidArgs<float> &, cudaStream_t);
-template cudaError_t col_fluid_launch<P2, false, true, LIM_HYBRID, true, false>(const ColFluidArgs<float> &, cudaStream_t);
+template cudaError_t col_fluid_launch<P2, false, 0, LIM_HYBRID, true, false>(const ColFluidArgs<float> &, cudaStream_t);
+template cudaError_t col_fluid_launch<P2, false, 1, LIM_HYBRID, true, false>(const ColFluidArgs<float> &, cudaStream_t);
+template cudaError_t col_fluid_launch<P2, false, 2, LIM_HYBRID, true, false>(const ColFluidArgs<float> &, cudaStream_t);
 }
