@@ -112,8 +112,14 @@ __global__ void __launch_bounds__(128, FISH_CT_MINB)
         Ab.hf = B.hf;
         Ab.ho = B.ho;
         Ab.dt = dt + B.box;
-        for (int g = 0; g < I.groups; ++g)
-            ct_columns<float, LIM, true>(Ab, (long long)I.first + 4ll * g + (threadIdx.x >> 5), threadIdx.x & 31);
+        // a group of four warps takes one segment of four consecutive rows
+        // (neighbour-row loads served from L1, as in the single-box kernel)
+        const long long nseg = (Ab.nf + 30) / 31;
+        for (int g = 0; g < I.groups; ++g) {
+            const long long q = (long long)I.first / 4 + g;
+            const long long ob = (q / nseg) * 4 + (threadIdx.x >> 5);
+            ct_columns<float, LIM, true>(Ab, ob * nseg + q % nseg, threadIdx.x & 31);
+        }
     }
 }
 
@@ -326,8 +332,8 @@ int build_tables(fish_batch *b)
                 BatchItem I{k, (int)(g0 * 128), (int)std::min<long long>(b->groups, fgroups - g0)};
                 fw.push_back({(long long)B.n * I.groups, I});
             }
-            const long long warps = (long long)((B.nf + 30) / 31) * B.no;   // 31 columns per warp
-            const long long cgroups = (warps + 3) / 4;
+            // 31 columns per warp; a group is one segment of four rows
+            const long long cgroups = (long long)((B.nf + 30) / 31) * ((B.no + 3) / 4);
             for (long long g0 = 0; g0 < cgroups; g0 += b->groups) {
                 BatchItem I{k, (int)(g0 * 4), (int)std::min<long long>(b->groups, cgroups - g0)};
                 cw.push_back({(long long)B.n * I.groups, I});
