@@ -65,14 +65,21 @@ enum {
     FISH_OPT_DX = 4,         /* cell widths; default 1/nx, 1/ny, 1/nz */
     FISH_OPT_DY = 5,
     FISH_OPT_DZ = 6,
-    FISH_OPT_GRAVITY = 7     /* FISH_GRAV_UNSPLIT (default): potential source terms inside L_d
+    FISH_OPT_GRAVITY = 7,    /* FISH_GRAV_UNSPLIT (default): potential source terms inside L_d
                                 (eq0253-eq0255); FISH_GRAV_SPLIT: L_d becomes G_d(dt/2) L_d G_d(dt/2)
                                 with G_d: m_d -= (dt/2) rho dphi/dx_d (centred difference) and E
                                 changed by the kinetic energy change (eq025111-eq02513).  Split
                                 gravity and FISH_OPT_HSE = 1 exclude each other (FISH_ERR_ARG).
                                 The kicks run inside the fluid sweep (separate passes on an
                                 irregular mesh). */
+    FISH_OPT_KERNELS = 8     /* kernel family of the FP32 fluid sweep (results are bitwise the
+                                same): FISH_KERNELS_COLUMN (default) the register-prefetch column
+                                march; FISH_KERNELS_RING the march fed through a shared-memory
+                                ring of TMA bulk copies (boxes whose fast extents are multiples of
+                                four, no potential, uniform mesh; elsewhere the column march).
+                                The ring is measured slower on GB300 and kept as an option. */
 };
+enum { FISH_KERNELS_COLUMN = 0, FISH_KERNELS_RING = 1 };
 enum { FISH_GRAV_UNSPLIT = 0, FISH_GRAV_SPLIT = 1 };
 enum { FISH_PREC_FP64 = 0, FISH_PREC_FP32 = 1 };
 enum { FISH_LIM_VANLEER = 0, FISH_LIM_MINMOD = 1, FISH_LIM_NONE = 2, FISH_LIM_HYBRID = 3 };

@@ -22,7 +22,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libfish.so")
 FISH_OK, FISH_ERR_ARG, FISH_ERR_CUDA, FISH_ERR_OOM, FISH_ERR_STATE, FISH_ERR_NONPHYSICAL, FISH_ERR_TIMEOUT = range(7)
 FISH_BC_PERIODIC, FISH_BC_OUTFLOW = 0, 1
 (FISH_OPT_PRECISION, FISH_OPT_LIMITER, FISH_OPT_HSE, FISH_OPT_PRED_DISS, FISH_OPT_DX, FISH_OPT_DY, FISH_OPT_DZ,
- FISH_OPT_GRAVITY) = range(8)
+ FISH_OPT_GRAVITY, FISH_OPT_KERNELS) = range(9)
+FISH_KERNELS_COLUMN, FISH_KERNELS_RING = 0, 1
 FISH_PREC_FP64, FISH_PREC_FP32 = 0, 1
 FISH_LIM_VANLEER, FISH_LIM_MINMOD, FISH_LIM_NONE, FISH_LIM_HYBRID = 0, 1, 2, 3
 FISH_GRAV_UNSPLIT, FISH_GRAV_SPLIT = 0, 1
@@ -124,7 +125,8 @@ class Box:
     (faces i+1/2), b_y (faces j+1/2), b_z (faces k+1/2)."""
 
     def __init__(self, nx, ny, nz, gamma, bc=FISH_BC_PERIODIC, precision="fp64", limiter=FISH_LIM_VANLEER,
-                 hse=False, pred_diss=1.0, h=None, use_torch_allocator=True, stream=None, gravity="unsplit"):
+                 hse=False, pred_diss=1.0, h=None, use_torch_allocator=True, stream=None, gravity="unsplit",
+                 kernels="column"):
         self._lib = load()
         self.n = (int(nx), int(ny), int(nz))
         self.precision = precision
@@ -144,6 +146,10 @@ class Box:
             self.set_option(FISH_OPT_GRAVITY, FISH_GRAV_SPLIT if gravity == "split" else FISH_GRAV_UNSPLIT)
             self.set_option(FISH_OPT_HSE, 1 if hse else 0)
             self.set_option(FISH_OPT_PRED_DISS, float(pred_diss))
+            if kernels not in ("column", "ring"):
+                raise ValueError("kernels must be 'column' or 'ring'")
+            if kernels == "ring":
+                self.set_option(FISH_OPT_KERNELS, FISH_KERNELS_RING)
             if h is not None:
                 for k, v in zip((FISH_OPT_DX, FISH_OPT_DY, FISH_OPT_DZ), h):
                     self.set_option(k, float(v))

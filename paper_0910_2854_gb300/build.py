@@ -9,6 +9,7 @@ Three translation units compiled in parallel, then linked:
   fish_capi.cu -- host-side C ABI
   fish_noalloc.cu -- the allocation-free diagnostics entry point
   fish_batch.cu -- batches of independent boxes (FP32)
+  fish_ring.cu -- FP32 sweeps fed through a shared-memory ring of bulk copies
 """
 from __future__ import annotations
 
@@ -34,6 +35,7 @@ UNITS = {
     "fish_capi.cu": [],
     "fish_noalloc.cu": [],
     "fish_batch.cu": ["-prec-sqrt=false", "-ftz=true"],
+    "fish_ring.cu": ["-prec-sqrt=false", "-ftz=true"],
 }
 
 

@@ -34,6 +34,7 @@ struct fish_ctx {
     int gsplit = 0;        // FISH_GRAV_SPLIT: gravity as G_d(dt/2) L_d G_d(dt/2)
     double alpha = 1.0;
     double h[3] = {0, 0, 0};
+    int kernels = FISH_KERNELS_COLUMN;  // FISH_OPT_KERNELS
 
     cudaStream_t own = nullptr;
     cudaStream_t stream = nullptr;
@@ -297,7 +298,8 @@ template <class T> int op_fluid(fish_ctx *c, int d, bool fuse_cfl)
     FISH_CK(c,
             Launch<T>::fluid(in, out, split ? nullptr : sweep_potential<T>(c, d), c->dt_dev,
                              geom(c), d, c->lim, c->hse != 0, c->gamma, c->alpha, c->h, c->flags,
-                             fuse_cfl ? c->minbits : nullptr, c->stream, mesh_of<T>(c).get(), fused_split),
+                             fuse_cfl ? c->minbits : nullptr, c->stream, mesh_of<T>(c).get(), fused_split,
+                             c->kernels),
             "fluid sweep launch");
     c->cu = 1 - c->cu;
     c->launches += 1;
@@ -472,6 +474,10 @@ int fish_set_option(fish_ctx *c, int key, double v)
         if (v != FISH_GRAV_UNSPLIT && v != FISH_GRAV_SPLIT) return fail(c, FISH_ERR_ARG, "bad gravity mode");
         if (v == FISH_GRAV_SPLIT && c->hse) return fail(c, FISH_ERR_ARG, "HSE correction needs unsplit gravity");
         c->gsplit = (int)v;
+        break;
+    case FISH_OPT_KERNELS:
+        if (v != FISH_KERNELS_COLUMN && v != FISH_KERNELS_RING) return fail(c, FISH_ERR_ARG, "bad kernel family");
+        c->kernels = (int)v;
         break;
     case FISH_OPT_PRED_DISS:
         if (!(v >= 0.0 && v <= 1.0)) return fail(c, FISH_ERR_ARG, "predictor factor outside [0,1]");

@@ -14,6 +14,18 @@ static inline unsigned col_grid(long long work, int block)
     return (unsigned)(g < 1 ? 1 : g);
 }
 
+// Whether every element index of a sweep over the box of A fits in an int
+// (with margin for the prefetch lines past the last column).
+template <class A_> static bool fits_int(const A_ &A)
+{
+#ifdef FISH_NO_I32
+    (void)A;
+    return false;
+#else
+    return A.off + (long long)A.nf * A.no * A.n + 1024 < (1ll << 31);
+#endif
+}
+
 // blocks of fluid_col_kernel: one thread per column group
 template <class V> static unsigned fluid_blocks(const ColFluidArgs<typename VT<V>::S> &A)
 {
@@ -30,13 +42,23 @@ cudaError_t col_fluid_launch(const ColFluidArgs<typename VT<V>::S> &A, cudaStrea
         fluid_col_kernel<V, HSE, GRAV, LIM, FT1, false, true><<<fluid_blocks<V>(A), 128, 0, s>>>(A);
         return cudaGetLastError();
     }
+    // the packed FP32 kernels index with int where the box allows it
+    constexpr bool I32 = std::is_same<V, P2>::value;
+    const bool small = I32 && fits_int(A);
     if constexpr (std::is_same<V, P2>::value && !HSE) {
         if (A.cfl_min) {
-            fluid_col_kernel<V, HSE, GRAV, LIM, FT1, true><<<fluid_blocks<V>(A), 128, 0, s>>>(A);
+            if (small) fluid_col_kernel<V, HSE, GRAV, LIM, FT1, true, false, int><<<fluid_blocks<V>(A), 128, 0, s>>>(A);
+            else fluid_col_kernel<V, HSE, GRAV, LIM, FT1, true><<<fluid_blocks<V>(A), 128, 0, s>>>(A);
             return cudaGetLastError();
         }
     }
     if (A.cfl_min) return cudaErrorInvalidValue;  // only the two-column kernels carry the CFL epilogue
+    if constexpr (I32) {
+        if (small) {
+            fluid_col_kernel<V, HSE, GRAV, LIM, FT1, false, false, int><<<fluid_blocks<V>(A), 128, 0, s>>>(A);
+            return cudaGetLastError();
+        }
+    }
     fluid_col_kernel<V, HSE, GRAV, LIM, FT1><<<fluid_blocks<V>(A), 128, 0, s>>>(A);
     return cudaGetLastError();
 }
@@ -107,6 +129,7 @@ cudaError_t col_ct_launch(const ColCTArgs<typename VT<V>::S> &A, cudaStream_t s)
     // one segment of FISH_CT_ROWS consecutive rows
     const int segc = 31 * VT<V>::W;
     const long long blocks = (long long)((A.nf + segc - 1) / segc) * ((A.no + FISH_CT_ROWS - 1) / FISH_CT_ROWS);
+    // (64-bit indices: int indices measured slower for this march)
     ct_col_kernel<V, LIM, FT1, NU><<<(unsigned)blocks, 32 * FISH_CT_ROWS, 0, s>>>(A);
     return cudaGetLastError();
 }

@@ -20,6 +20,8 @@
 // Both operators read the current buffers and write the other ones.
 #pragma once
 
+#include <type_traits>
+
 #include "fish_math.cuh"
 #include "fish_types.h"
 #include "fish_vec.cuh"
@@ -415,21 +417,55 @@ template <class V> struct FMarch {
     V dprev;             // split gravity: potential (FP64) or its difference (FP32) of raw cell r-1
 };
 
-template <class S> struct FCtx {
-    long long base;      // offset of cell 0 of the first column
-    long long ofm;       // offset of the fast-axis face below the first column
-    long long oom;       // offset of the other-axis face below (mapped)
+// IX: element index type (int where every index of the launch fits, else
+// long long): a load then costs one wide multiply-add for its address.
+template <class S, class IX = long long> struct FCtx {
+    IX base;             // offset of cell 0 of the first column
+    IX ofm;              // offset of the fast-axis face below the first column
+    IX oom;              // offset of the other-axis face below (mapped)
 };
+
+// L2 prefetch of one cell of a warp's march with a single instruction: lane
+// l takes field row l / 2 (u0..u4, b_d, b_f, b_o, b_o of the row below, the
+// potential) and the (l % 2)-th 128-byte line of the warp's span of it in
+// cell 0, shifted by whole cells along the sweep (when the stride along the
+// sweep is not a multiple of a line the lines drift by less than one line:
+// it is a hint).
+#ifndef FISH_FL_PF_WARP
+#define FISH_FL_PF_WARP 1
+#endif
+template <class S, class IX> struct FPf {
+    const S *p;   // the lane's line in cell 0 (nullptr: lane idle); cell c: p + c * sd
+};
+
+template <class S, class IX>
+__device__ __forceinline__ void fpf_setup(const ColFluidArgs<S> &A, const S *bfp, const S *bop, IX base0, IX oom0,
+                                          int span, bool grav, int lane, FPf<S, IX> &P)
+{
+    P.p = nullptr;
+    const int r = lane >> 1;
+    if (r >= (grav ? 10 : 9)) return;
+    const S *f = r < 5 ? A.u[r] : (r == 5 ? A.bd : (r == 6 ? bfp : (r == 9 ? A.phi : bop)));
+    const IX r0 = base0 + (r == 8 ? oom0 : (IX)0);
+    const IX line = (r0 & ~(IX)31) + (IX)(32 * (lane & 1));
+    if (line <= r0 + (IX)(span - 1)) P.p = f + line;
+}
+
+template <class S, class IX>
+__device__ __forceinline__ void fpf_step(const ColFluidArgs<S> &A, const FPf<S, IX> &P, int c)
+{
+    if (P.p) pf_l2(P.p + (IX)c * (IX)A.sd);
+}
 
 // load raw cell s (any s): every index through the boundary map; a ghost
 // cell copies the mapped cell as a whole, its lower b_d face included
-template <class V, bool GRAV, bool FT1>
-__device__ __forceinline__ void fload_mapped(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S> &X,
-                                             int s, FRaw<V> &R)
+template <class V, bool GRAV, bool FT1, class IX = long long>
+__device__ __forceinline__ void fload_mapped(const ColFluidArgs<typename VT<V>::S> &A,
+                                             const FCtx<typename VT<V>::S, IX> &X, int s, FRaw<V> &R)
 {
     const int cc = gmap(s, A.n, A.bc);
-    const long long i = X.base + (long long)cc * A.sd;
-    const long long im = X.base + (long long)gmap(cc - 1, A.n, A.bc) * A.sd;
+    const IX i = X.base + (IX)cc * (IX)A.sd;
+    const IX im = X.base + (IX)gmap(cc - 1, A.n, A.bc) * (IX)A.sd;
     const auto *bfp = FT1 ? A.bt1 : A.bt2;
     const auto *bop = FT1 ? A.bt2 : A.bt1;
 #pragma unroll
@@ -453,9 +489,9 @@ __device__ __forceinline__ void fload_mapped(const ColFluidArgs<typename VT<V>::
 
 // load interior cell at element offset i (no map; its lower b_d face is the
 // upper face of the previous cell, set by the caller)
-template <class V, bool GRAV, bool FT1>
-__device__ __forceinline__ void fload_direct(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S> &X,
-                                             long long i, FRaw<V> &R)
+template <class V, bool GRAV, bool FT1, class IX = long long>
+__device__ __forceinline__ void fload_direct(const ColFluidArgs<typename VT<V>::S> &A,
+                                             const FCtx<typename VT<V>::S, IX> &X, IX i, FRaw<V> &R)
 {
     const auto *bfp = FT1 ? A.bt1 : A.bt2;
     const auto *bop = FT1 ? A.bt2 : A.bt1;
@@ -478,9 +514,9 @@ __device__ __forceinline__ void fload_direct(const ColFluidArgs<typename VT<V>::
 #define FISH_FL_PF_NEIGH 1   // also the lower other-axis face (a neighbour row)
 #endif
 // prefetch into L2 the fields the fluid march will load for interior cell i
-template <class V, bool GRAV, bool FT1>
-__device__ __forceinline__ void fprefetch(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S> &X,
-                                          long long i)
+template <class V, bool GRAV, bool FT1, class IX = long long>
+__device__ __forceinline__ void fprefetch(const ColFluidArgs<typename VT<V>::S> &A,
+                                          const FCtx<typename VT<V>::S, IX> &X, IX i)
 {
     const auto *bfp = FT1 ? A.bt1 : A.bt2;
     const auto *bop = FT1 ? A.bt2 : A.bt1;
@@ -526,19 +562,19 @@ template <class V> __device__ __forceinline__ void sg_kick(V u[5], V dk, V tau)
 // Centred potential difference (eq02513) of the image cell of ghost r (its
 // copy along d): FP64 from the potential, FP32 from the stored differences
 // D_c = phi_{c+1} - phi_c (D_{-1} = 0 at an outflow boundary).
-template <class V>
-__device__ __forceinline__ V sg_image_dk(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S> &X,
-                                         int r, V rtwoh)
+template <class V, class IX = long long>
+__device__ __forceinline__ V sg_image_dk(const ColFluidArgs<typename VT<V>::S> &A,
+                                         const FCtx<typename VT<V>::S, IX> &X, int r, V rtwoh)
 {
     const int cc = gmap(r, A.n, A.bc);
     if constexpr (VT<V>::F64) {
-        const V pp = vload<V>(A.phi, X.base + (long long)gmap(cc + 1, A.n, A.bc) * A.sd);
-        const V pm = vload<V>(A.phi, X.base + (long long)gmap(cc - 1, A.n, A.bc) * A.sd);
+        const V pp = vload<V>(A.phi, X.base + (IX)gmap(cc + 1, A.n, A.bc) * (IX)A.sd);
+        const V pm = vload<V>(A.phi, X.base + (IX)gmap(cc - 1, A.n, A.bc) * (IX)A.sd);
         return (pp - pm) / (2.0 * A.h);
     } else {
-        const V dc = vload<V>(A.phi, X.base + (long long)cc * A.sd);
+        const V dc = vload<V>(A.phi, X.base + (IX)cc * (IX)A.sd);
         V dl = vb<V>(0.0f);
-        if (cc > 0 || A.bc == BC_PERIODIC) dl = vload<V>(A.phi, X.base + (long long)gmap(cc - 1, A.n, A.bc) * A.sd);
+        if (cc > 0 || A.bc == BC_PERIODIC) dl = vload<V>(A.phi, X.base + (IX)gmap(cc - 1, A.n, A.bc) * (IX)A.sd);
         return (dc + dl) * rtwoh;
     }
 }
@@ -547,9 +583,10 @@ __device__ __forceinline__ V sg_image_dk(const ColFluidArgs<typename VT<V>::S> &
 // operator-split kicks G_d(dt/2) folded into the march (eq025111): the raw
 // cell is kicked as it is consumed, the output cell's old state before its
 // update and the result after it (reading C-22 for the kick).
-template <class V, bool HSE, int GM, int LIM, bool FT1, bool CFLF, bool NU, int K, int ST, int LD>
-__device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S> &X,
-                                      FMarch<V> &M, int r, V lam, V lamh, V hdt, V dt, V rtwoh)
+template <class V, bool HSE, int GM, int LIM, bool FT1, bool CFLF, bool NU, int K, int ST, int LD, class IX = long long>
+__device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S, IX> &X,
+                                      FMarch<V> &M, int r, V lam, V lamh, V hdt, V dt, V rtwoh,
+                                      const FPf<typename VT<V>::S, IX> &PF)
 {
     constexpr bool GRAV = GM == 1, SG = GM == 2, PHI = GM != 0;
     constexpr int k2 = K & 1, p2 = (K + 1) & 1;
@@ -580,19 +617,20 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
     }
     // prefetch raw cell r+1
     if constexpr (LD == LD_DIRECT || LD == LD_DIRECT_PF) {
-        fload_direct<V, PHI, FT1>(A, X, X.base + (long long)(r + 1) * A.sd, M.R);
+        fload_direct<V, PHI, FT1, IX>(A, X, X.base + (IX)(r + 1) * (IX)A.sd, M.R);
         if constexpr (NU) M.R.w = A.wd[r + 1];
         M.R.bdm = bd_r;
         if constexpr (LD == LD_DIRECT_PF) {
             const int pf = min(r + 1 + FISH_PF_DIST, A.n - 1);
-            fprefetch<V, PHI, FT1>(A, X, X.base + (long long)pf * A.sd);
+            if constexpr (FISH_FL_PF_WARP) fpf_step(A, PF, pf);
+            else fprefetch<V, PHI, FT1, IX>(A, X, X.base + (IX)pf * (IX)A.sd);
         }
     } else if constexpr (LD == LD_MAPPED) {
-        fload_mapped<V, PHI, FT1>(A, X, r + 1, M.R);
+        fload_mapped<V, PHI, FT1, IX>(A, X, r + 1, M.R);
     }
     // old state of the output cell o = r-3
     const int o = r - 3;
-    const long long io = X.base + (long long)o * A.sd;
+    const IX io = X.base + (IX)o * (IX)A.sd;
     V un[5];
     if constexpr ((ST & ST_OUT) != 0) {
 #pragma unroll
@@ -603,7 +641,7 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
         // takes its image cell's), and of the output cell's old state
         V dk;
         if (r < 0 || r >= A.n) {
-            dk = sg_image_dk<V>(A, X, r, rtwoh);
+            dk = sg_image_dk<V, IX>(A, X, r, rtwoh);
         } else if constexpr (VT<V>::F64) {
             dk = (M.R.phi - M.dprev) / (2.0 * A.h);  // phi_{r+1} - phi_{r-1}
         } else {
@@ -693,7 +731,7 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
                     // CFL rate of the updated cell with its cell-centred field
                     const auto *bfp = FT1 ? A.bt1 : A.bt2;
                     const auto *bop = FT1 ? A.bt2 : A.bt1;
-                    const long long iom = X.base + (long long)(o > 0 ? o - 1 : gmap(-1, A.n, A.bc)) * A.sd;
+                    const IX iom = X.base + (IX)(o > 0 ? o - 1 : gmap(-1, A.n, A.bc)) * (IX)A.sd;
                     V bc[3];
                     bc[0] = half * (vload<V>(A.bd, iom) + vload<V>(A.bd, io));
                     const V bfv = vload<V>(bfp, io);
@@ -719,16 +757,17 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
 
 // L_d over all columns.  The prologue runs raw cells -3 .. 2 (K = 1, 2, 3,
 // 0, 1, 2); boxes with n < 8 load everything through the map.
-template <class V, bool HSE, int GRAV, int LIM, bool FT1, bool CFLF, bool NU, int PLD>
-__device__ __forceinline__ void fprologue(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S> &X,
-                                          FMarch<V> &M, V lam, V lamh, V hdt, V dt, V rtwoh)
+template <class V, bool HSE, int GRAV, int LIM, bool FT1, bool CFLF, bool NU, int PLD, class IX = long long>
+__device__ __forceinline__ void fprologue(const ColFluidArgs<typename VT<V>::S> &A,
+                                          const FCtx<typename VT<V>::S, IX> &X, FMarch<V> &M, V lam, V lamh, V hdt,
+                                          V dt, V rtwoh, const FPf<typename VT<V>::S, IX> &PF)
 {
-    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, 0, LD_MAPPED>(A, X, M, -3, lam, lamh, hdt, dt, rtwoh);
-    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ST_F1, LD_MAPPED>(A, X, M, -2, lam, lamh, hdt, dt, rtwoh);
-    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ST_F1 | ST_PRED, PLD>(A, X, M, -1, lam, lamh, hdt, dt, rtwoh);
-    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ST_F1 | ST_PRED, PLD>(A, X, M, 0, lam, lamh, hdt, dt, rtwoh);
-    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ST_F1 | ST_PRED, PLD>(A, X, M, 1, lam, lamh, hdt, dt, rtwoh);
-    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ST_F1 | ST_PRED | ST_F2, PLD>(A, X, M, 2, lam, lamh, hdt, dt, rtwoh);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, 0, LD_MAPPED, IX>(A, X, M, -3, lam, lamh, hdt, dt, rtwoh, PF);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ST_F1, LD_MAPPED, IX>(A, X, M, -2, lam, lamh, hdt, dt, rtwoh, PF);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ST_F1 | ST_PRED, PLD, IX>(A, X, M, -1, lam, lamh, hdt, dt, rtwoh, PF);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ST_F1 | ST_PRED, PLD, IX>(A, X, M, 0, lam, lamh, hdt, dt, rtwoh, PF);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ST_F1 | ST_PRED, PLD, IX>(A, X, M, 1, lam, lamh, hdt, dt, rtwoh, PF);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ST_F1 | ST_PRED | ST_F2, PLD, IX>(A, X, M, 2, lam, lamh, hdt, dt, rtwoh, PF);
 }
 
 #ifndef FISH_COL_MINB
@@ -739,7 +778,7 @@ __device__ __forceinline__ void fprologue(const ColFluidArgs<typename VT<V>::S> 
 #endif
 
 // The march of thread cid (column group cid of the box described by A).
-template <class V, bool HSE, int GRAV, int LIM, bool FT1, bool CFLF, bool NU = false>
+template <class V, bool HSE, int GRAV, int LIM, bool FT1, bool CFLF, bool NU = false, class IX = long long>
 __device__ __forceinline__ void fluid_columns(const ColFluidArgs<typename VT<V>::S> &A, long long cid)
 {
     using S = typename VT<V>::S;
@@ -748,10 +787,21 @@ __device__ __forceinline__ void fluid_columns(const ColFluidArgs<typename VT<V>:
     if (cid >= (long long)cols * A.no) return;
     const int fp = (int)(cid % cols), ob = (int)(cid / cols);
     const int f0 = fp * W;
-    FCtx<S> X;
-    X.base = A.off + (long long)f0 + (long long)ob * A.so;
-    X.ofm = (long long)(gmap(f0 - 1, A.nf, A.bc) - f0);
-    X.oom = (long long)(gmap(ob - 1, A.no, A.bc) - ob) * A.so;
+    FCtx<S, IX> X;
+    X.base = (IX)A.off + (IX)f0 + (IX)ob * (IX)A.so;
+    X.ofm = (IX)(gmap(f0 - 1, A.nf, A.bc) - f0);
+    X.oom = (IX)(gmap(ob - 1, A.no, A.bc) - ob) * (IX)A.so;
+    // per-warp L2 prefetch over the span of the warp's first lane (32 groups
+    // of W columns; a warp that crosses a row end prefetches its first row)
+    FPf<S, IX> PF;
+    {
+        const unsigned am = __activemask();
+        const int l0 = __ffs(am) - 1;
+        const IX b0 = __shfl_sync(am, X.base, l0);
+        const IX m0 = __shfl_sync(am, X.oom, l0);
+        const int span = min(32 * W, A.nf - (int)(b0 - (IX)A.off) % A.nf);
+        fpf_setup(A, FT1 ? A.bt1 : A.bt2, FT1 ? A.bt2 : A.bt1, b0, m0, span, GRAV != 0, (int)(threadIdx.x & 31), PF);
+    }
     const double dtd = *A.dt;
     const V dt = vb<V>(S(dtd));
     const V lam = vb<V>(S(dtd / A.h));
@@ -767,31 +817,31 @@ __device__ __forceinline__ void fluid_columns(const ColFluidArgs<typename VT<V>:
     M.ph[0] = M.ph[1] = vb<V>(0.0f);
     M.w0 = M.w1 = M.w2 = M.w3 = M.w4 = typename VT<V>::S(1);
     M.dprev = vb<V>(0.0f);
-    fload_mapped<V, GRAV != 0, FT1>(A, X, -3, M.R);
+    fload_mapped<V, GRAV != 0, FT1, IX>(A, X, -3, M.R);
     constexpr int ALL = ST_F1 | ST_PRED | ST_F2 | ST_OUT;
     int r = 3;
     if (n >= 8) {
-        fprologue<V, HSE, GRAV, LIM, FT1, CFLF, NU, LD_DIRECT>(A, X, M, lam, lamh, hdt, dt, rtwoh);
+        fprologue<V, HSE, GRAV, LIM, FT1, CFLF, NU, LD_DIRECT, IX>(A, X, M, lam, lamh, hdt, dt, rtwoh, PF);
         // steady state: the four steps r .. r+3 prefetch interior cells
 #pragma unroll 1
         for (; r + 4 <= n - 1; r += 4) {
-            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ALL, LD_DIRECT_PF>(A, X, M, r, lam, lamh, hdt, dt, rtwoh);
-            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ALL, LD_DIRECT_PF>(A, X, M, r + 1, lam, lamh, hdt, dt, rtwoh);
-            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ALL, LD_DIRECT_PF>(A, X, M, r + 2, lam, lamh, hdt, dt, rtwoh);
-            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ALL, LD_DIRECT_PF>(A, X, M, r + 3, lam, lamh, hdt, dt, rtwoh);
+            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ALL, LD_DIRECT_PF, IX>(A, X, M, r, lam, lamh, hdt, dt, rtwoh, PF);
+            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ALL, LD_DIRECT_PF, IX>(A, X, M, r + 1, lam, lamh, hdt, dt, rtwoh, PF);
+            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ALL, LD_DIRECT_PF, IX>(A, X, M, r + 2, lam, lamh, hdt, dt, rtwoh, PF);
+            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ALL, LD_DIRECT_PF, IX>(A, X, M, r + 3, lam, lamh, hdt, dt, rtwoh, PF);
         }
     } else {
-        fprologue<V, HSE, GRAV, LIM, FT1, CFLF, NU, LD_MAPPED>(A, X, M, lam, lamh, hdt, dt, rtwoh);
+        fprologue<V, HSE, GRAV, LIM, FT1, CFLF, NU, LD_MAPPED, IX>(A, X, M, lam, lamh, hdt, dt, rtwoh, PF);
     }
     // tail: raw cells r .. n+2 (r = 3 mod 4, at most seven), loads through
     // the map (harmless beyond n+2)
-    if (r <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ALL, LD_MAPPED>(A, X, M, r, lam, lamh, hdt, dt, rtwoh);
-    if (r + 1 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ALL, LD_MAPPED>(A, X, M, r + 1, lam, lamh, hdt, dt, rtwoh);
-    if (r + 2 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ALL, LD_MAPPED>(A, X, M, r + 2, lam, lamh, hdt, dt, rtwoh);
-    if (r + 3 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ALL, LD_MAPPED>(A, X, M, r + 3, lam, lamh, hdt, dt, rtwoh);
-    if (r + 4 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ALL, LD_MAPPED>(A, X, M, r + 4, lam, lamh, hdt, dt, rtwoh);
-    if (r + 5 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ALL, LD_MAPPED>(A, X, M, r + 5, lam, lamh, hdt, dt, rtwoh);
-    if (r + 6 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ALL, LD_NONE>(A, X, M, r + 6, lam, lamh, hdt, dt, rtwoh);
+    if (r <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ALL, LD_MAPPED, IX>(A, X, M, r, lam, lamh, hdt, dt, rtwoh, PF);
+    if (r + 1 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ALL, LD_MAPPED, IX>(A, X, M, r + 1, lam, lamh, hdt, dt, rtwoh, PF);
+    if (r + 2 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ALL, LD_MAPPED, IX>(A, X, M, r + 2, lam, lamh, hdt, dt, rtwoh, PF);
+    if (r + 3 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ALL, LD_MAPPED, IX>(A, X, M, r + 3, lam, lamh, hdt, dt, rtwoh, PF);
+    if (r + 4 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ALL, LD_MAPPED, IX>(A, X, M, r + 4, lam, lamh, hdt, dt, rtwoh, PF);
+    if (r + 5 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ALL, LD_MAPPED, IX>(A, X, M, r + 5, lam, lamh, hdt, dt, rtwoh, PF);
+    if (r + 6 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ALL, LD_NONE, IX>(A, X, M, r + 6, lam, lamh, hdt, dt, rtwoh, PF);
     const unsigned fl = checks_flags(M.chk);
     if (fl) atomicOr(A.flags, fl);
     if constexpr (CFLF) {
@@ -813,11 +863,11 @@ __device__ __forceinline__ void fluid_columns(const ColFluidArgs<typename VT<V>:
     }
 }
 
-template <class V, bool HSE, int GRAV, int LIM, bool FT1, bool CFLF = false, bool NU = false>
+template <class V, bool HSE, int GRAV, int LIM, bool FT1, bool CFLF = false, bool NU = false, class IX = long long>
 __global__ void __launch_bounds__(128, VT<V>::F64 ? 1 : (VT<V>::W == 2 || HSE ? FISH_COL_MINB : FISH_COL_MINB1))
     fluid_col_kernel(const ColFluidArgs<typename VT<V>::S> A)
 {
-    fluid_columns<V, HSE, GRAV, LIM, FT1, CFLF, NU>(A, (long long)blockIdx.x * blockDim.x + threadIdx.x);
+    fluid_columns<V, HSE, GRAV, LIM, FT1, CFLF, NU, IX>(A, (long long)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -937,10 +987,12 @@ __device__ __forceinline__ void cface(CFace<V> &P, V vt, V bf, V lamh, V lam, V 
 // lane beneath it, whose edge flux arrives by a warp shuffle.  Raw inputs of
 // cell s+1 are loaded while cell s is computed.
 // ---------------------------------------------------------------------------
-template <class S> struct CTCtx {
-    long long base;      // element offset of the lane's first column in cell 0
-    long long ofp;       // offset to the fast-axis column above the lane's last column
-    long long oom, oop;  // offsets to the other-axis rows below / above (mapped)
+// IX: element index type (int where every index of the launch fits, else
+// long long); a load then costs one wide multiply-add for its address.
+template <class S, class IX = long long> struct CTCtx {
+    IX base;             // element offset of the lane's first column in cell 0
+    IX ofp;              // offset to the fast-axis column above the lane's last column
+    IX oom, oop;         // offsets to the other-axis rows below / above (mapped)
     bool active;         // lane stores its columns
     bool fixy;           // halo lane at an outflow edge: its upper column is a copy of the lower
     S wfa, wfb;          // irregular mesh: widths of the lane's column and the one above (fast axis)
@@ -964,12 +1016,12 @@ template <class V> __device__ __forceinline__ void fixy_(V &a, bool f)
 
 // load the raw inputs of cell s (MAPPED: s through the boundary map; OUTLD:
 // also b_d of the output cell s-4, which is interior)
-template <class V, bool MAPPED, bool OUTLD, bool NU>
-__device__ __forceinline__ void ctload(const ColCTArgs<typename VT<V>::S> &A, const CTCtx<typename VT<V>::S> &X, int s,
-                                       CTRaw<V> &R)
+template <class V, bool MAPPED, bool OUTLD, bool NU, class IX = long long>
+__device__ __forceinline__ void ctload(const ColCTArgs<typename VT<V>::S> &A, const CTCtx<typename VT<V>::S, IX> &X,
+                                       int s, CTRaw<V> &R)
 {
     const int sm = MAPPED ? gmap(s, A.n, A.bc) : s;
-    const long long i = X.base + (long long)sm * A.sd;
+    const IX i = X.base + (IX)sm * (IX)A.sd;
     if constexpr (NU) R.w = A.wd[sm];  // a ghost has the width of its image (reading C-23)
     R.rc = vload<V>(A.rho, i);
     R.mc = vload<V>(A.md, i);
@@ -989,7 +1041,7 @@ __device__ __forceinline__ void ctload(const ColCTArgs<typename VT<V>::S> &A, co
         }
     }
     // (the tail's last step loads one cell past the march: keep its index in range)
-    if constexpr (OUTLD) R.bdo = vload<V>(A.bd, X.base + (long long)(MAPPED ? min(s - 4, A.n - 1) : s - 4) * A.sd);
+    if constexpr (OUTLD) R.bdo = vload<V>(A.bd, X.base + (IX)(MAPPED ? min(s - 4, A.n - 1) : s - 4) * (IX)A.sd);
 }
 
 // prefetch into L2 the fields of interior cell i (the neighbour rows too
@@ -1001,9 +1053,9 @@ __device__ __forceinline__ void ctload(const ColCTArgs<typename VT<V>::S> &A, co
 #ifndef FISH_CT_PF_NEIGH
 #define FISH_CT_PF_NEIGH 1
 #endif
-template <class V>
-__device__ __forceinline__ void ctprefetch(const ColCTArgs<typename VT<V>::S> &A, const CTCtx<typename VT<V>::S> &X,
-                                           long long i)
+template <class V, class IX = long long>
+__device__ __forceinline__ void ctprefetch(const ColCTArgs<typename VT<V>::S> &A,
+                                           const CTCtx<typename VT<V>::S, IX> &X, IX i)
 {
     pf_l2(A.rho + i);
     pf_l2(A.md + i);
@@ -1019,11 +1071,54 @@ __device__ __forceinline__ void ctprefetch(const ColCTArgs<typename VT<V>::S> &A
     pf_l2(A.bd + i);
 }
 
+// FP32 one-column CT (uniform mesh): the two face pencils above a column,
+// along the fast and the other axis, have the same update; they advance
+// together as one packed pencil (component x: fast axis, y: other axis),
+// so one FP32x2 instruction serves both.
+#ifndef FISH_CT_PACK
+#define FISH_CT_PACK 1
+#endif
+template <class V, bool NU> constexpr bool ct_packs() { return FISH_CT_PACK && std::is_same<V, float>::value && !NU; }
+
 template <class V> struct CTMarch {
     CFace<V> PF, PO, POm;   // fast-axis faces above, other-axis faces above / below
+    CFace<P2> PFO;          // packed PF (x) and PO (y) of the FP32 one-column march
     CTRaw<V> R;             // raw inputs of the next cell
     CWid<V> cw;             // irregular mesh: widths along d of cells s-1 .. s-5
 };
+
+// L2 prefetch of one cell of a warp's march with a single instruction: lane
+// l < 30 takes field row l / 3 of the ten the march reads (rho, m_d of this
+// row and the rows below / above, b_o of the row below, b_f, b_o, b_d of this
+// row) and the (l % 3)-th 128-byte line of the warp's span of that row.
+#ifndef FISH_CT_PF_WARP
+#define FISH_CT_PF_WARP 0   // measured slower than the per-field prefetch for this march
+#endif
+template <class S, class IX> struct CTPf {
+    const S *p;   // the lane's line in cell 0 (nullptr: lane idle); cell c: p + c * sd
+};
+
+template <class S, class IX>
+__device__ __forceinline__ void ctpf_setup(const ColCTArgs<S> &A, const CTCtx<S, IX> &X0, int c0, int c1, int lane,
+                                           CTPf<S, IX> &P)
+{
+    P.p = nullptr;
+    if (lane >= 30) return;
+    const int r = lane / 3;
+    // rows 0..5: rho, m_d of this row, the row below, the row above; 6: b_o
+    // below; 7, 8, 9: b_f, b_o, b_d of this row (selects, no local array)
+    const S *f = r == 6 || r == 8 ? A.bo : (r == 7 ? A.bf : (r == 9 ? A.bd : ((r & 1) ? A.md : A.rho)));
+    const IX ro = (r == 2 || r == 3 || r == 6) ? X0.oom : ((r == 4 || r == 5) ? X0.oop : (IX)0);
+    const IX r0 = X0.base + ro + (IX)c0;
+    const IX line = (r0 & ~(IX)31) + (IX)(32 * (lane % 3));
+    if (line <= X0.base + ro + (IX)c1) P.p = f + line;
+}
+
+template <class S, class IX>
+__device__ __forceinline__ void ctpf_step(const ColCTArgs<S> &A, const CTPf<S, IX> &P, int s)
+{
+    if (P.p) pf_l2(P.p + (IX)s * (IX)A.sd);
+}
 
 template <class V> __device__ __forceinline__ V shfl_up1(V a)
 {
@@ -1038,9 +1133,11 @@ enum : int { CL_NONE = 0, CL_DIRECT = 1, CL_DIRECT_PF = 2, CL_MAPPED = 3 };
 
 // One cell s of the CT march (K = s mod 4); the raw inputs of s are in M.R.
 // Next loads cell s+1 (kind LD; NOUT: with b_d of cell s-3 for its output).
-template <class V, int LIM, bool FT1, bool NU, int K, bool PRE1, bool PRE2, bool CORR, bool OUT, int LD, bool NOUT>
-__device__ __forceinline__ void ctstep(const ColCTArgs<typename VT<V>::S> &A, const CTCtx<typename VT<V>::S> &X,
-                                       CTMarch<V> &M, int s, V lamh, V lam, V lamf, V lamo, V dt)
+template <class V, int LIM, bool FT1, bool NU, int K, bool PRE1, bool PRE2, bool CORR, bool OUT, int LD, bool NOUT,
+          class IX = long long>
+__device__ __forceinline__ void ctstep(const ColCTArgs<typename VT<V>::S> &A, const CTCtx<typename VT<V>::S, IX> &X,
+                                       CTMarch<V> &M, int s, V lamh, V lam, V lamf, V lamo, V dt,
+                                       const CTPf<typename VT<V>::S, IX> &PF)
 {
     // widths of cells s .. s-5 for this step (the width of cell s arrived
     // with its raw inputs)
@@ -1063,11 +1160,14 @@ __device__ __forceinline__ void ctstep(const ColCTArgs<typename VT<V>::S> &A, co
     const V bdo = M.R.bdo;
     // load cell s+1
     if constexpr (LD == CL_DIRECT || LD == CL_DIRECT_PF) {
-        ctload<V, false, NOUT, NU>(A, X, s + 1, M.R);
-        if constexpr (LD == CL_DIRECT_PF)
-            ctprefetch<V>(A, X, X.base + (long long)min(s + 1 + FISH_CT_PF_DIST, A.n - 1) * A.sd);
+        ctload<V, false, NOUT, NU, IX>(A, X, s + 1, M.R);
+        if constexpr (LD == CL_DIRECT_PF) {
+            const int pfc = min(s + 1 + FISH_CT_PF_DIST, A.n - 1);
+            if constexpr (FISH_CT_PF_WARP) ctpf_step(A, PF, pfc);
+            else ctprefetch<V, IX>(A, X, X.base + (IX)pfc * (IX)A.sd);
+        }
     } else if constexpr (LD == CL_MAPPED) {
-        ctload<V, true, NOUT, NU>(A, X, s + 1, M.R);
+        ctload<V, true, NOUT, NU, IX>(A, X, s + 1, M.R);
     }
     const V half = vb<V>(0.5f);
     // face velocities (eq0361): the mean of the two cells across the face,
@@ -1087,22 +1187,38 @@ __device__ __forceinline__ void ctstep(const ColCTArgs<typename VT<V>::S> &A, co
         vtOm = vdiv(vfma(V(X.woa), vom, V(X.wom) * vc), V(X.wom + X.woa));
     }
     V nF, nO, dummy;
-    cface<V, LIM, K, PRE1, PRE2, CORR, OUT, NU>(M.PF, vtF, bF, lamh, lam, nF, A.lim, M.cw, dt);
-    cface<V, LIM, K, PRE1, PRE2, CORR, OUT, NU>(M.PO, vtO, bO, lamh, lam, nO, A.lim, M.cw, dt);
+    constexpr bool PK = ct_packs<V, NU>();
+    if constexpr (PK) {
+        P2 n2;
+        cface<P2, LIM, K, PRE1, PRE2, CORR, OUT, false>(M.PFO, P2{make_float2(vtF, vtO)}, P2{make_float2(bF, bO)},
+                                                        vb<P2>(lamh), vb<P2>(lam), n2, A.lim);
+        nF = n2.v.x;
+        nO = n2.v.y;
+    } else {
+        cface<V, LIM, K, PRE1, PRE2, CORR, OUT, NU>(M.PF, vtF, bF, lamh, lam, nF, A.lim, M.cw, dt);
+        cface<V, LIM, K, PRE1, PRE2, CORR, OUT, NU>(M.PO, vtO, bO, lamh, lam, nO, A.lim, M.cw, dt);
+    }
     cface<V, LIM, K, PRE1, PRE2, CORR, false, NU>(M.POm, vtOm, bOm, lamh, lam, dummy, A.lim, M.cw, dt);
     if constexpr (OUT) {
         constexpr int e = K & 1;
         // edge flux of the fast-axis face below: the upper pencil of the lane beneath
-        const V fup = M.PF.f[e];
+        V fup, fpo;
+        if constexpr (PK) {
+            fup = M.PFO.f[e].v.x;
+            fpo = M.PFO.f[e].v.y;
+        } else {
+            fup = M.PF.f[e];
+            fpo = M.PO.f[e];
+        }
         const V sh = shfl_up1(fup);
         V fdn;
         if constexpr (VT<V>::W == 2) fdn = vshift_lo(sh.v.y, fup);
         else fdn = sh;
         if (X.active) {
-            const long long io = X.base + (long long)(s - 4) * A.sd;
+            const IX io = X.base + (IX)(s - 4) * (IX)A.sd;
             vstore(A.bfo, io, nF);
             vstore(A.boo, io, nO);
-            const V tF = fup - fdn, tO = M.PO.f[e] - M.POm.f[e];
+            const V tF = fup - fdn, tO = fpo - M.POm.f[e];
             V r;
             if constexpr (VT<V>::F64) {
                 if constexpr (FT1) r = bdo + lamf * tF + lamo * tO;
@@ -1118,13 +1234,16 @@ __device__ __forceinline__ void ctstep(const ColCTArgs<typename VT<V>::S> &A, co
 #ifndef FISH_CT_MINB
 #define FISH_CT_MINB 4
 #endif
+#ifndef FISH_CT_MINB2
+#define FISH_CT_MINB2 1   // FP64 and two-column CT blocks per SM (register bound)
+#endif
 
 // B_d over all columns (eq0350 advection of the transverse components,
 // eq0360 constraint update of b_d from the same edge fluxes).  Every lane of
 // a warp takes the same steps (shuffles); lanes without columns of their
 // own repeat a valid column and store nothing.
 // The march of warp gw (31 W columns of one row) of the box described by A.
-template <class V, int LIM, bool FT1, bool NU = false>
+template <class V, int LIM, bool FT1, bool NU = false, class IX = long long>
 __device__ __forceinline__ void ct_columns(const ColCTArgs<typename VT<V>::S> &A, long long gw, int lane)
 {
     using S = typename VT<V>::S;
@@ -1134,7 +1253,7 @@ __device__ __forceinline__ void ct_columns(const ColCTArgs<typename VT<V>::S> &A
     if (gw >= (long long)nseg * A.no) return;  // whole warps only
     const int seg = (int)(gw % nseg), ob = (int)(gw / nseg);
     int cl = seg * SEGC + (lane - 1) * W;       // first logical column of the lane
-    CTCtx<S> X;
+    CTCtx<S, IX> X;
     X.active = lane >= 1 && cl < A.nf;
     if (lane >= 1 && cl >= A.nf) cl = A.nf - W;  // idle lane: repeat a valid column
     int cb;                                      // physical first column
@@ -1148,10 +1267,20 @@ __device__ __forceinline__ void ct_columns(const ColCTArgs<typename VT<V>::S> &A
         X.fixy = W == 2;
     }
     const int cfp = gmap(cl + W, A.nf, A.bc);
-    X.base = A.off + (long long)cb + (long long)ob * A.so;
-    X.ofp = (long long)(cfp - cb);
-    X.oom = (long long)(gmap(ob - 1, A.no, A.bc) - ob) * A.so;
-    X.oop = (long long)(gmap(ob + 1, A.no, A.bc) - ob) * A.so;
+    X.base = (IX)A.off + (IX)cb + (IX)ob * (IX)A.so;
+    X.ofp = (IX)(cfp - cb);
+    X.oom = (IX)(gmap(ob - 1, A.no, A.bc) - ob) * (IX)A.so;
+    X.oop = (IX)(gmap(ob + 1, A.no, A.bc) - ob) * (IX)A.so;
+    // per-warp L2 prefetch: the span of physical columns the warp reads
+    // (halo column to the column above the last lane's), clipped to the row
+    CTPf<S, IX> PFw;
+    {
+        CTCtx<S, IX> X0 = X;
+        X0.base = (IX)A.off + (IX)ob * (IX)A.so;
+        const int c0 = max(seg * SEGC - W, 0);
+        const int c1 = min(seg * SEGC + SEGC, A.nf - 1);
+        ctpf_setup(A, X0, c0, c1, lane, PFw);
+    }
     const double dtd = *A.dt;
     const V dtv = vb<V>(S(dtd));
     const V lamh = vb<V>(S(dtd / (2.0 * A.h)));
@@ -1178,47 +1307,52 @@ __device__ __forceinline__ void ct_columns(const ColCTArgs<typename VT<V>::S> &A
         for (int k = 0; k < 4; ++k) z.vt[k] = z.vh[k] = z.bf[k] = z.wp[k] = vb<V>(0.0f);
         z.w[0] = z.w[1] = z.f1[0] = z.f1[1] = z.f[0] = z.f[1] = vb<V>(0.0f);
         M.PF = M.PO = M.POm = z;
+        CFace<P2> z2;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) z2.vt[k] = z2.vh[k] = z2.bf[k] = z2.wp[k] = vb<P2>(0.0f);
+        z2.w[0] = z2.w[1] = z2.f1[0] = z2.f1[1] = z2.f[0] = z2.f[1] = vb<P2>(0.0f);
+        M.PFO = z2;
     }
     M.R.bdo = vb<V>(0.0f);
     M.cw.w0 = M.cw.w1 = M.cw.w2 = M.cw.w3 = M.cw.w4 = M.cw.w5 = vb<V>(1.0f);
-    ctload<V, true, false, NU>(A, X, -4, M.R);
+    ctload<V, true, false, NU, IX>(A, X, -4, M.R);
     // prologue s = -4 .. 3 (stages switch on at -1, 0, 3); cells 0 .. 3 are
     // loaded directly when n >= 4
-    ctstep<V, LIM, FT1, NU, 0, false, false, false, false, CL_MAPPED, false>(A, X, M, -4, lamh, lam, lamf, lamo, dtv);
-    ctstep<V, LIM, FT1, NU, 1, false, false, false, false, CL_MAPPED, false>(A, X, M, -3, lamh, lam, lamf, lamo, dtv);
-    ctstep<V, LIM, FT1, NU, 2, false, false, false, false, CL_MAPPED, false>(A, X, M, -2, lamh, lam, lamf, lamo, dtv);
+    ctstep<V, LIM, FT1, NU, 0, false, false, false, false, CL_MAPPED, false, IX>(A, X, M, -4, lamh, lam, lamf, lamo, dtv, PFw);
+    ctstep<V, LIM, FT1, NU, 1, false, false, false, false, CL_MAPPED, false, IX>(A, X, M, -3, lamh, lam, lamf, lamo, dtv, PFw);
+    ctstep<V, LIM, FT1, NU, 2, false, false, false, false, CL_MAPPED, false, IX>(A, X, M, -2, lamh, lam, lamf, lamo, dtv, PFw);
     int s = 4;
     if (n >= 8) {
-        ctstep<V, LIM, FT1, NU, 3, true, false, false, false, CL_DIRECT, false>(A, X, M, -1, lamh, lam, lamf, lamo, dtv);
-        ctstep<V, LIM, FT1, NU, 0, true, true, false, false, CL_DIRECT, false>(A, X, M, 0, lamh, lam, lamf, lamo, dtv);
-        ctstep<V, LIM, FT1, NU, 1, true, true, false, false, CL_DIRECT, false>(A, X, M, 1, lamh, lam, lamf, lamo, dtv);
-        ctstep<V, LIM, FT1, NU, 2, true, true, false, false, CL_DIRECT, false>(A, X, M, 2, lamh, lam, lamf, lamo, dtv);
-        ctstep<V, LIM, FT1, NU, 3, true, true, true, false, CL_DIRECT, true>(A, X, M, 3, lamh, lam, lamf, lamo, dtv);
+        ctstep<V, LIM, FT1, NU, 3, true, false, false, false, CL_DIRECT, false, IX>(A, X, M, -1, lamh, lam, lamf, lamo, dtv, PFw);
+        ctstep<V, LIM, FT1, NU, 0, true, true, false, false, CL_DIRECT, false, IX>(A, X, M, 0, lamh, lam, lamf, lamo, dtv, PFw);
+        ctstep<V, LIM, FT1, NU, 1, true, true, false, false, CL_DIRECT, false, IX>(A, X, M, 1, lamh, lam, lamf, lamo, dtv, PFw);
+        ctstep<V, LIM, FT1, NU, 2, true, true, false, false, CL_DIRECT, false, IX>(A, X, M, 2, lamh, lam, lamf, lamo, dtv, PFw);
+        ctstep<V, LIM, FT1, NU, 3, true, true, true, false, CL_DIRECT, true, IX>(A, X, M, 3, lamh, lam, lamf, lamo, dtv, PFw);
         // steady state: the four steps s .. s+3 load interior cells s+1 .. s+4
 #pragma unroll 1
         for (; s + 4 <= n - 1; s += 4) {
-            ctstep<V, LIM, FT1, NU, 0, true, true, true, true, CL_DIRECT_PF, true>(A, X, M, s, lamh, lam, lamf, lamo, dtv);
-            ctstep<V, LIM, FT1, NU, 1, true, true, true, true, CL_DIRECT_PF, true>(A, X, M, s + 1, lamh, lam, lamf, lamo, dtv);
-            ctstep<V, LIM, FT1, NU, 2, true, true, true, true, CL_DIRECT_PF, true>(A, X, M, s + 2, lamh, lam, lamf, lamo, dtv);
-            ctstep<V, LIM, FT1, NU, 3, true, true, true, true, CL_DIRECT_PF, true>(A, X, M, s + 3, lamh, lam, lamf, lamo, dtv);
+            ctstep<V, LIM, FT1, NU, 0, true, true, true, true, CL_DIRECT_PF, true, IX>(A, X, M, s, lamh, lam, lamf, lamo, dtv, PFw);
+            ctstep<V, LIM, FT1, NU, 1, true, true, true, true, CL_DIRECT_PF, true, IX>(A, X, M, s + 1, lamh, lam, lamf, lamo, dtv, PFw);
+            ctstep<V, LIM, FT1, NU, 2, true, true, true, true, CL_DIRECT_PF, true, IX>(A, X, M, s + 2, lamh, lam, lamf, lamo, dtv, PFw);
+            ctstep<V, LIM, FT1, NU, 3, true, true, true, true, CL_DIRECT_PF, true, IX>(A, X, M, s + 3, lamh, lam, lamf, lamo, dtv, PFw);
         }
     } else {
-        ctstep<V, LIM, FT1, NU, 3, true, false, false, false, CL_MAPPED, false>(A, X, M, -1, lamh, lam, lamf, lamo, dtv);
-        ctstep<V, LIM, FT1, NU, 0, true, true, false, false, CL_MAPPED, false>(A, X, M, 0, lamh, lam, lamf, lamo, dtv);
-        ctstep<V, LIM, FT1, NU, 1, true, true, false, false, CL_MAPPED, false>(A, X, M, 1, lamh, lam, lamf, lamo, dtv);
-        ctstep<V, LIM, FT1, NU, 2, true, true, false, false, CL_MAPPED, false>(A, X, M, 2, lamh, lam, lamf, lamo, dtv);
-        ctstep<V, LIM, FT1, NU, 3, true, true, true, false, CL_MAPPED, true>(A, X, M, 3, lamh, lam, lamf, lamo, dtv);
+        ctstep<V, LIM, FT1, NU, 3, true, false, false, false, CL_MAPPED, false, IX>(A, X, M, -1, lamh, lam, lamf, lamo, dtv, PFw);
+        ctstep<V, LIM, FT1, NU, 0, true, true, false, false, CL_MAPPED, false, IX>(A, X, M, 0, lamh, lam, lamf, lamo, dtv, PFw);
+        ctstep<V, LIM, FT1, NU, 1, true, true, false, false, CL_MAPPED, false, IX>(A, X, M, 1, lamh, lam, lamf, lamo, dtv, PFw);
+        ctstep<V, LIM, FT1, NU, 2, true, true, false, false, CL_MAPPED, false, IX>(A, X, M, 2, lamh, lam, lamf, lamo, dtv, PFw);
+        ctstep<V, LIM, FT1, NU, 3, true, true, true, false, CL_MAPPED, true, IX>(A, X, M, 3, lamh, lam, lamf, lamo, dtv, PFw);
     }
     // tail: cells s .. n+3 through the map (n-4 <= s <= n-1 after the loop,
     // s = 0 mod 4: at most eight cells)
-    if (s <= n + 3) ctstep<V, LIM, FT1, NU, 0, true, true, true, true, CL_MAPPED, true>(A, X, M, s, lamh, lam, lamf, lamo, dtv);
-    if (s + 1 <= n + 3) ctstep<V, LIM, FT1, NU, 1, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 1, lamh, lam, lamf, lamo, dtv);
-    if (s + 2 <= n + 3) ctstep<V, LIM, FT1, NU, 2, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 2, lamh, lam, lamf, lamo, dtv);
-    if (s + 3 <= n + 3) ctstep<V, LIM, FT1, NU, 3, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 3, lamh, lam, lamf, lamo, dtv);
-    if (s + 4 <= n + 3) ctstep<V, LIM, FT1, NU, 0, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 4, lamh, lam, lamf, lamo, dtv);
-    if (s + 5 <= n + 3) ctstep<V, LIM, FT1, NU, 1, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 5, lamh, lam, lamf, lamo, dtv);
-    if (s + 6 <= n + 3) ctstep<V, LIM, FT1, NU, 2, true, true, true, true, CL_MAPPED, true>(A, X, M, s + 6, lamh, lam, lamf, lamo, dtv);
-    if (s + 7 <= n + 3) ctstep<V, LIM, FT1, NU, 3, true, true, true, true, CL_NONE, false>(A, X, M, s + 7, lamh, lam, lamf, lamo, dtv);
+    if (s <= n + 3) ctstep<V, LIM, FT1, NU, 0, true, true, true, true, CL_MAPPED, true, IX>(A, X, M, s, lamh, lam, lamf, lamo, dtv, PFw);
+    if (s + 1 <= n + 3) ctstep<V, LIM, FT1, NU, 1, true, true, true, true, CL_MAPPED, true, IX>(A, X, M, s + 1, lamh, lam, lamf, lamo, dtv, PFw);
+    if (s + 2 <= n + 3) ctstep<V, LIM, FT1, NU, 2, true, true, true, true, CL_MAPPED, true, IX>(A, X, M, s + 2, lamh, lam, lamf, lamo, dtv, PFw);
+    if (s + 3 <= n + 3) ctstep<V, LIM, FT1, NU, 3, true, true, true, true, CL_MAPPED, true, IX>(A, X, M, s + 3, lamh, lam, lamf, lamo, dtv, PFw);
+    if (s + 4 <= n + 3) ctstep<V, LIM, FT1, NU, 0, true, true, true, true, CL_MAPPED, true, IX>(A, X, M, s + 4, lamh, lam, lamf, lamo, dtv, PFw);
+    if (s + 5 <= n + 3) ctstep<V, LIM, FT1, NU, 1, true, true, true, true, CL_MAPPED, true, IX>(A, X, M, s + 5, lamh, lam, lamf, lamo, dtv, PFw);
+    if (s + 6 <= n + 3) ctstep<V, LIM, FT1, NU, 2, true, true, true, true, CL_MAPPED, true, IX>(A, X, M, s + 6, lamh, lam, lamf, lamo, dtv, PFw);
+    if (s + 7 <= n + 3) ctstep<V, LIM, FT1, NU, 3, true, true, true, true, CL_NONE, false, IX>(A, X, M, s + 7, lamh, lam, lamf, lamo, dtv, PFw);
 }
 
 // The warps of a block take the same segment of FISH_CT_ROWS consecutive
@@ -1229,14 +1363,14 @@ __device__ __forceinline__ void ct_columns(const ColCTArgs<typename VT<V>::S> &A
 #ifndef FISH_CT_ROWS
 #define FISH_CT_ROWS 8   // rows (warps) per CT block
 #endif
-template <class V, int LIM, bool FT1, bool NU = false>
-__global__ void __launch_bounds__(32 * FISH_CT_ROWS, VT<V>::F64 ? 1 : FISH_CT_MINB * 4 / FISH_CT_ROWS)
+template <class V, int LIM, bool FT1, bool NU = false, class IX = long long>
+__global__ void __launch_bounds__(32 * FISH_CT_ROWS, (VT<V>::F64 || VT<V>::W == 2) ? FISH_CT_MINB2 : FISH_CT_MINB * 4 / FISH_CT_ROWS)
     ct_col_kernel(const ColCTArgs<typename VT<V>::S> A)
 {
     constexpr int SEGC = 31 * VT<V>::W;
     const long long nseg = (A.nf + SEGC - 1) / SEGC;
     const long long seg = blockIdx.x % nseg, ob = (blockIdx.x / nseg) * FISH_CT_ROWS + (threadIdx.x >> 5);
-    ct_columns<V, LIM, FT1, NU>(A, ob * nseg + seg, threadIdx.x & 31);
+    ct_columns<V, LIM, FT1, NU, IX>(A, ob * nseg + seg, threadIdx.x & 31);
 }
 
 // ---------------------------------------------------------------------------
@@ -1250,5 +1384,10 @@ template <class V>
 cudaError_t col_fluid(const ColFluidArgs<typename VT<V>::S> &A, bool hse, bool ft1, cudaStream_t s);
 // B_d with the lane-vector type V.
 template <class V> cudaError_t col_ct(const ColCTArgs<typename VT<V>::S> &A, bool ft1, cudaStream_t s);
+// L_d fed by a shared-memory ring of bulk copies (fish_ring.cu): FP32 pairs,
+// t1 fast, no potential, uniform mesh, Van Leer / minmod / hybrid limiter,
+// nf % 4 == 0 and 16-byte aligned rows.  cudaErrorNotSupported where it
+// does not apply (the caller then runs the column kernel).
+cudaError_t ring_fluid(const ColFluidArgs<float> &A, cudaStream_t s);
 
 }  // namespace fish

@@ -63,7 +63,7 @@ template <class T>
 cudaError_t Launch<T>::fluid(const T *const in[8], T *const out[5], const T *phi, const double *dt,
                              const Geom &g, int d, int lim, bool hse, double gamma, double alpha,
                              const double h3[3], unsigned *flags, unsigned long long *cfl_min, cudaStream_t s,
-                             const T *const *w3, bool split_gravity)
+                             const T *const *w3, bool split_gravity, int kernels)
 {
     // split gravity: phi drives kicks G_d(dt/2) folded into the march
     // (uniform meshes with a potential, no hydrostatic correction)
@@ -111,8 +111,15 @@ cudaError_t Launch<T>::fluid(const T *const in[8], T *const out[5], const T *phi
     if constexpr (sizeof(T) == 8) {
         return col_fluid<double>(A, hse, F.ft1, s);
     } else {
-        // two columns per thread (packed FP32x2) when the fast extent is even
-        if (uses_pairs<T>(F, lim, hse, w3 != nullptr)) return col_fluid<P2>(A, hse, true, s);
+        // two columns per thread (packed FP32x2) when the fast extent is even;
+        // the ring-fed march if asked for and it applies
+        if (uses_pairs<T>(F, lim, hse, w3 != nullptr)) {
+            if (kernels == 1) {
+                const cudaError_t e = ring_fluid(A, s);
+                if (e != cudaErrorNotSupported) return e;
+            }
+            return col_fluid<P2>(A, hse, true, s);
+        }
         return col_fluid<float>(A, hse, true, s);
     }
 }

@@ -13,12 +13,13 @@ template <class T> struct Launch {
     // L_d: in[8] current state, out[5] fluid fields of the other buffer.
     // With cfl_min, the sweep also reduces the CFL rate of its output state
     // (all three axes, cell widths h3) into *cfl_min (only where
-    // fluid_fuses_cfl says so).  w3: nullptr (uniform mesh) or the device
+    // fluid_fuses_cfl says so).  kernels: 0 the register-prefetch column
+    // marches, 1 the shared-memory ring march where it applies.  w3: nullptr (uniform mesh) or the device
     // arrays of cell widths along x, y, z (irregular mesh, eq037).
     static cudaError_t fluid(const T *const in[8], T *const out[5], const T *phi, const double *dt,
                              const Geom &g, int d, int lim, bool hse, double gamma, double alpha,
                              const double h3[3], unsigned *flags, unsigned long long *cfl_min, cudaStream_t s,
-                             const T *const *w3 = nullptr, bool split_gravity = false);
+                             const T *const *w3 = nullptr, bool split_gravity = false, int kernels = 0);
     static bool fluid_fuses_cfl(const Geom &g, int d, int lim, bool hse);
     // B_d: rho, m_d of the current state; b[3] current field, bout[3] other.
     static cudaError_t ct(const T *rho, const T *md, const T *const b[3], T *const bout[3],
