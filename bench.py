@@ -66,6 +66,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--no-same-box", action="store_true",
+                   help="skip the FP64 run of the workload's own box (like-for-like FP32/FP64 ratio and L1(rho))")
     p.add_argument("--oracle-sample", type=float, default=None,
                    help="print only the oracle's rate on the 128^3 twin within this many seconds (the "
                         "single-core leg runs itself this way with OMP_NUM_THREADS=1)")
@@ -276,15 +278,15 @@ def time_operators(F, box, torch, reps=3):
 
 
 # DRAM bytes per cell of one launch of each kernel kind, from the ncu
-# capture summarised in profiles/sweeps_f32_turbulence_384.md (384^3 launch,
-# dram__bytes_read.sum + dram__bytes_write.sum over its cells).  Set an entry
-# to None when that kernel changes until it is captured again.
-TRAFFIC_B_PER_CELL = {"fluid": 52.2, "ct": 32.1}
+# capture of the 384^3 turbulence box (dram__bytes_read.sum +
+# dram__bytes_write.sum over its cells).  Set an entry to None when that
+# kernel changes until it is captured again.
+TRAFFIC_B_PER_CELL = {"fluid": None, "ct": None}
 
 
 # FP64 pipe instructions (DADD + DMUL + DFMA, thread level) per cell of one
-# launch of each FP64 kernel kind, from the ncu capture summarised in
-# profiles/sweeps_f64_orszag_tang_128.md (Orszag-Tang 128^3).  The FP64 path
+# launch of each FP64 kernel kind, from the ncu capture of the Orszag-Tang
+# 128^3 box.  The FP64 path
 # is bound by GB300's FP64 pipe, so its roofline is this rate against the
 # probed FMA rate of the device (fish_probe_fp64_fma).
 FP64_OPS_PER_CELL = {"fluid": 537, "ct": 170}
@@ -295,24 +297,22 @@ def traffic_per_cell(kernel_key):
 
 
 def e2e_rate(F, box, torch, n, steps):
-    """End to end through the public API: every step uploads the state from
-    pinned host memory (FP32, the path's arithmetic type), advances one
-    double step and reads back the step's CFL time step (8 bytes)."""
+    """End to end through the public API, a full host round trip per step:
+    upload the whole state from pinned host memory (fish_set_state_host,
+    FP32, the path's arithmetic type), advance one double step with the
+    device CFL, and download the whole new state into the same pinned buffer
+    (fish_get_state_host, which also returns any device error)."""
     N = n ** 3
     host = torch.empty((8, n, n, n), dtype=torch.float32, pin_memory=True)
-    dev = torch.empty((8, n, n, n), dtype=torch.float32, device="cuda")
-    box.get_state_device(dev)
-    host.copy_(dev)
-    del dev
-    torch.cuda.empty_cache()
+    box.get_state_host(host)
     t0 = time.perf_counter()
     for _ in range(steps):
         box.set_state_host(host)
         box.step_cfl(CFL, 1)
-        box.last_dt()
+        box.get_state_host(host)
     el = time.perf_counter() - t0
     del host
-    return N * steps / el, 32 * N, 8
+    return N * steps / el, 32 * N, 32 * N
 
 
 def run_fish(args, rank, world, local):
@@ -382,12 +382,25 @@ def run_fish(args, rank, world, local):
             peak64 = F.probe_fp64_fma()
             ach64 = FP64_OPS_PER_CELL[key64.split("_")[0]] * n64 / (ops64[key64] * 1e-3)
             fp64 = {"workload": FP64_WORKLOAD["workload"], "value": v64, "unit": UNIT, "ms_per_step": ms64 / k64,
-                    "fp32_over_fp64": (value / world) / v64,
+                    "fp32_turbulence_over_fp64_orszag_tang": (value / world) / v64,
                     "roofline": {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "FP64 pipe op/s",
                                  "frac": ach64 / peak64, "kernel": key64, "kernel_ms": ops64[key64],
                                  "ops_per_cell": FP64_OPS_PER_CELL[key64.split("_")[0]],
                                  "peak_source": "probed (fish_probe_fp64_fma)", "op_ms": ops64}}
             b64.close()
+            torch.cuda.empty_cache()
+            if not args.no_same_box:
+                # like for like: the same turbulence box advanced in FP64 (3
+                # double steps each way from the same initial state)
+                from paper_0910_2854_gb300 import reports
+                sb = reports.fp32_vs_fp64(n, steps=3, k=CFL)
+                fp64["same_box"] = {
+                    "workload": WORKLOAD["workload"].replace("FP32 bulk with compensated pressure recovery and "
+                                                             "FP64 reductions", "FP64 throughout"),
+                    "fp64_ms_per_step": sb["fp64"]["ms_per_step"], "fp64_value": sb["fp64"]["cell_updates_per_s"],
+                    "fp32_over_fp64": (value / world) / sb["fp64"]["cell_updates_per_s"],
+                    "l1_rho_rel_fp32_vs_fp64": sb["l1_rho_rel"], "steps_compared": 3}
+                torch.cuda.empty_cache()
         batch = None
         if not args.no_batch:
             from paper_0910_2854_gb300 import reports

@@ -167,6 +167,12 @@ int fish_apply(fish_ctx *ctx, int op, int dir, double dt);
 /* Download the state to a host buffer of 8*nx*ny*nz doubles.  Synchronises. */
 int fish_get_state(fish_ctx *ctx, double *state);
 
+/* Download the state to a host buffer of dtype FISH_F64 or FISH_F32 (same
+ * layout; pinned host memory gives full copy bandwidth), converting on the
+ * device where the context precision differs.  Synchronises and returns
+ * pending device errors, like fish_get_state. */
+int fish_get_state_host(fish_ctx *ctx, void *state, int dtype);
+
 /* Copy the state into a device buffer of dtype FISH_F64 / FISH_F32.  Queued
  * on the stream; returns pending device errors only after fish_sync. */
 int fish_get_state_device(fish_ctx *ctx, void *state, int dtype);
@@ -258,9 +264,10 @@ void fish_batch_destroy(fish_batch *b);
  * every GPU loading the library keeps until exit; nz > 4096 is rejected
  * with FISH_ERR_ARG.  All calls share it and each call rewrites the rows it
  * uses, so calls whose kernels overlap on the GPU (unordered streams) race:
- * order them.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Allocates nothing (no cudaMalloc, no
+ * order them.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress) with the caller's device current, so a device reset
+ * between calls is followed; the first call on a device may load the
+ * library's device code, so make that first call before any stream capture.  Allocates nothing (no cudaMalloc, no
  * allocator callback).  Returns FISH_ERR_ARG for bad arguments and
  * FISH_ERR_CUDA if a launch fails. */
 int fish_diagnostics_noalloc(const void *state, int dtype, int nx, int ny, int nz, int bc, double dx,

@@ -14,7 +14,11 @@ Parity status of the functions (what pins each one; see ``tests/test_oracle_*``)
     solution, the circularly polarised Alfven wave after one period,
     second-order convergence on smooth advection, conservation and
     div b = 0 to round-off, axis-permutation symmetry and the limiter-off
-    reduction to the textbook Rusanov predictor-corrector.
+    reduction to the textbook Rusanov predictor-corrector; the constrained
+    transport's upwind predictor and face-velocity smoothing (eq0362-eq0364)
+    by closed forms of the linearised operator: the amplification factor of
+    a single field mode in a uniform flow and the cos^2(theta/2) transfer
+    function of the smoothing in the response to a velocity mode.
   * hydrostatic-gradient correction (``hse=True``): pinned by a discrete
     hydrostatic atmosphere, in which the corrected acoustic dissipation of
     the mass flux vanishes; the polytrope behaviour of the paper's Sec. 4 is
@@ -31,9 +35,9 @@ Parity status of the functions (what pins each one; see ``tests/test_oracle_*``)
     totals and of the per-cell-width divergence, a uniform state staying
     uniform, exact free fall in a linear potential (split and unsplit), the
     commutation with a reflection of state and mesh, exact shear-flow face
-    velocities and the closed-form CFL step.  Parity unpinned: the weights
-    of the edge-velocity interpolation along the sweep (they only decide the
-    upwind side where the smoothed face velocity changes sign).
+    velocities, the closed-form CFL step and, for the edge-velocity weights
+    along the sweep, the upwind choice at an interface where the linearly
+    interpolated velocity changes sign.
   * ``test_oracle_mutants.py`` plants mistakes in a copy of the source and
     checks that the pins catch each of them.
 """

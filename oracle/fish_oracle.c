@@ -20,9 +20,7 @@
  *   - B_d: constrained transport (eq0330-eq0364);
  *   - CFL time step (eq0083-eq0084);
  *   - irregular Cartesian meshes (Sec. 2.5, eq037, eq0420): cell widths per
- *     axis, readings C-23 .. C-27 (the edge-velocity weights of C-27 are
- *     parity unpinned: they only decide the upwind side where the smoothed
- *     face velocity changes sign).
+ *     axis, readings C-23 .. C-27.
  * Equations are cited by the paper's LaTeX labels.
  * Where the paper is silent, garbled or inconsistent, the reading used is
  * named C-n in the comments; each is listed with its justification in the

@@ -34,7 +34,7 @@ FISH_BATCH_OPT_LIMITER, FISH_BATCH_OPT_ORDER, FISH_BATCH_OPT_GROUPS, FISH_BATCH_
 # every symbol include/fish.h declares (checked by the CPU test suite)
 EXPORTS = ("fish_create", "fish_set_option", "fish_set_stream", "fish_set_allocator", "fish_set_state",
            "fish_set_state_device", "fish_set_state_host", "fish_set_potential", "fish_set_mesh", "fish_cfl_dt", "fish_step", "fish_step_cfl",
-           "fish_last_dt", "fish_apply", "fish_get_state", "fish_get_state_device", "fish_diagnostics",
+           "fish_last_dt", "fish_apply", "fish_get_state", "fish_get_state_host", "fish_get_state_device", "fish_diagnostics",
            "fish_sync", "fish_clear_error", "fish_last_error", "fish_launch_count", "fish_destroy",
            "fish_diagnostics_noalloc", "fish_probe_fp64_fma", "fish_batch_create", "fish_batch_set_option", "fish_batch_set_stream",
            "fish_batch_set_state", "fish_batch_step", "fish_batch_get_state", "fish_batch_last_dt",
@@ -84,6 +84,7 @@ def load(path: str = LIB_PATH):
             "fish_apply": ([P, ctypes.c_int, ctypes.c_int, ctypes.c_double], ctypes.c_int),
             "fish_get_state": ([P, D], ctypes.c_int),
             "fish_get_state_device": ([P, P, ctypes.c_int], ctypes.c_int),
+            "fish_get_state_host": ([P, P, ctypes.c_int], ctypes.c_int),
             "fish_diagnostics": ([P, D], ctypes.c_int),
             "fish_sync": ([P], ctypes.c_int),
             "fish_clear_error": ([P], ctypes.c_int),
@@ -304,6 +305,23 @@ class Box:
     def get_state(self):
         out = np.empty((8, self.n[2], self.n[1], self.n[0]), dtype=np.float64)
         self._check(self._lib.fish_get_state(self.ctx, _dptr(out)), "fish_get_state")
+        return out
+
+    def get_state_host(self, out):
+        """Download into a host buffer (contiguous CPU torch tensor, ideally
+        pinned, or numpy array), float64 or float32, converted on the device."""
+        if hasattr(out, "data_ptr"):
+            import torch
+            if out.dtype not in (torch.float64, torch.float32) or not out.is_contiguous():
+                raise ValueError("host state must be a contiguous float64/float32 tensor")
+            ptr, dt, size = out.data_ptr(), (FISH_F64 if out.dtype == torch.float64 else FISH_F32), out.numel()
+        else:
+            if out.dtype not in (np.float64, np.float32) or not out.flags.c_contiguous:
+                raise ValueError("host state must be a contiguous float64/float32 array")
+            ptr, dt, size = out.ctypes.data, (FISH_F64 if out.dtype == np.float64 else FISH_F32), out.size
+        if size != 8 * np.prod(self.n):
+            raise ValueError("state has %d values, expected %d" % (size, 8 * np.prod(self.n)))
+        self._check(self._lib.fish_get_state_host(self.ctx, ctypes.c_void_p(ptr), dt), "fish_get_state_host")
         return out
 
     def get_state_device(self, out):

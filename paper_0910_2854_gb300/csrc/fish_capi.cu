@@ -835,6 +835,35 @@ int fish_get_state(fish_ctx *c, double *state)
     return check_flags(c);
 }
 
+int fish_get_state_host(fish_ctx *c, void *state, int dtype)
+{
+    if (!c || !state || (dtype != FISH_F64 && dtype != FISH_F32)) return FISH_ERR_ARG;
+    if (dtype == FISH_F64) return fish_get_state(c, (double *)state);
+    int r = ready(c);
+    if (r) return r;
+    if ((r = set_layout(c, 0))) return r;
+    if (c->prec == FISH_PREC_FP32) {
+        for (int f = 0; f < 8; ++f)
+            FISH_CK(c, cudaMemcpyAsync((float *)state + (long long)f * c->N, field_ptr(c, f), c->N * sizeof(float),
+                                       cudaMemcpyDeviceToHost, c->stream),
+                    "state download");
+    } else {
+        if ((r = ensure_stage(c))) return r;
+        float *stage = (float *)c->stage;
+        for (int f = 0; f < 8; ++f)
+            for (long long o = 0; o < c->N; o += kStageChunk) {
+                const long long m = c->N - o < kStageChunk ? c->N - o : kStageChunk;
+                FISH_CK(c, Launch<double>::to_f32((const double *)field_ptr(c, f) + o, stage, m, c->stream),
+                        "convert");
+                c->launches += 1;
+                FISH_CK(c, cudaMemcpyAsync((float *)state + (long long)f * c->N + o, stage, m * sizeof(float),
+                                           cudaMemcpyDeviceToHost, c->stream),
+                        "state download");
+            }
+    }
+    return check_flags(c);
+}
+
 int fish_get_state_device(fish_ctx *c, void *state, int dtype)
 {
     int r = ready(c);

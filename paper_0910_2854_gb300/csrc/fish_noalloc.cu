@@ -19,44 +19,34 @@
 //   - two calls whose kernels overlap on the GPU (different streams, no
 //     ordering between them) race on the array and may return wrong
 //     results: order them on one stream or synchronise in between;
-//   - the device address of the array is looked up once per device, on the
-//     first call made with that device current (cudaGetSymbolAddress); make
-//     that first call outside any stream capture.
+//   - the device address of the array is looked up on every call
+//     (cudaGetSymbolAddress, with the caller's device current), so a device
+//     reset between calls, which loads the module anew, is followed; the
+//     first call on a device may load the module, so make it outside any
+//     stream capture.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "../../include/fish.h"
 
 namespace {
 
 constexpr int kMaxPlanes = 4096;
-constexpr int kMaxDevices = 64;
 constexpr int kThreads = 256;
 
 // per-plane partial results: sums of the 8 fields, then max |div b|
 static __device__ __align__(256) double g_plane_partials[kMaxPlanes * 9];
 
-std::mutex g_mu;
-double *g_scratch[kMaxDevices] = {};
-
-// Device address of g_plane_partials on the current device (looked up once
-// per device).  Host code must not pass the symbol itself to a kernel: on
-// the host it names a stand-in, not device memory.
+// Device address of g_plane_partials on the current device, looked up on
+// every call (cheap once the module is loaded; a cached address would go
+// stale if the caller reset the device in between).  Host code must not pass
+// the symbol itself to a kernel: on the host it names a stand-in, not device
+// memory.
 cudaError_t scratch_for_current_device(double **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_plane_partials);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_plane_partials);
-        if (e != cudaSuccess) return e;
-        g_scratch[dev] = static_cast<double *>(p);
-    }
-    *out = g_scratch[dev];
+    *out = static_cast<double *>(p);
     return cudaSuccess;
 }
 

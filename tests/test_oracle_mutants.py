@@ -3,14 +3,13 @@ a dropped term, a wrong index, a transposed operand) in a copy of the oracle
 source, compile it, and check that the pin battery rejects every mutant.
 The unmodified oracle must pass the same battery.
 
-Not in the list, because no fixed point we have tells them apart from the
-paper's method (they are "parity unpinned" details):
-  * a downwind instead of upwind first-order predictor flux in the
-    constrained transport: still a consistent first-order predictor feeding
-    the upwinded TVD corrector (smooth orders, conservation, div b and the
-    total variation of an advected square wave are all unchanged);
-  * dropping the [1,2,1] smoothing of the face velocity (eq0362): an O(h^2)
-    change added for stability, invisible on smooth solutions."""
+The details of the constrained transport that no convergence order,
+conservation law or divergence check tells apart -- the upwind (not
+downwind) first-order predictor, the [1,2,1] smoothing of the face velocity
+(eq0362) and, on an irregular mesh, the weights of the edge velocity
+(reading C-27) -- are caught by closed forms of the linearised operator
+(``test_oracle_pins.py``: mode amplification factor, smoothing transfer
+function, upwind choice at a sign change of the interpolated velocity)."""
 import math
 
 import numpy as np
@@ -49,6 +48,10 @@ MUTANTS = {
     "field_not_centred": ("bc3[ax] = 0.5 * (q[5 + ax][or_index(P, cm[0], cm[1], cm[2])] + q[5 + ax][idx]);",
                           "bc3[ax] = q[5 + ax][idx];"),
     "hse_sign": ("ddu[k] = or_minmod(du[k] - gk, du[k]);", "ddu[k] = or_minmod(du[k] + gk, du[k]);"),
+    "ct_predictor_downwind": ("f1[e] = vbar > 0.0 ? w[e] : w[e + 1];", "f1[e] = vbar > 0.0 ? w[e + 1] : w[e];"),
+    "ct_smoothing_dropped": ("vh[e] = 0.25 * (vt[e + 1] + 2.0 * vt[e] + vt[e - 1]);", "vh[e] = vt[e];"),
+    "nu_edge_velocity_weights_swapped": ("return (wb * va + wa * vb) / (wa + wb);",
+                                         "return (wa * va + wb * vb) / (wa + wb);"),
 }
 
 
@@ -279,13 +282,26 @@ def battery(oracle_mod, lib):
         from test_oracle_pins import face_velocity_case
         return face_velocity_case(oracle_mod, lib)
 
+    def ct_mode():
+        from test_oracle_pins import ct_upwind_mode_case
+        return ct_upwind_mode_case(oracle_mod, lib)
+
+    def ct_smoothing():
+        from test_oracle_pins import ct_smoothing_case
+        return ct_smoothing_case(oracle_mod, lib)
+
+    def nu_ct_edge():
+        from test_oracle_pins import ct_edge_velocity_case
+        return ct_edge_velocity_case(oracle_mod, lib)
+
     for name, fn in [("alfven", alfven), ("oblique", oblique), ("fastwave", fastwave),
                      ("entropy", entropy), ("sod", sod),
                      ("invariants", invariants), ("freefall", freefall), ("cfl", cfl),
                      ("atmosphere", atmosphere), ("rusanov", rusanov), ("uniform", uniform),
                      ("hybrid", hybrid), ("splitfall", splitfall), ("nu_uniform", nu_uniform),
                      ("nu_conserve", nu_conserve), ("nu_mirror", nu_mirror), ("nu_freefall", nu_freefall),
-                     ("nu_face_velocity", nu_face_velocity)]:
+                     ("nu_face_velocity", nu_face_velocity), ("ct_mode", ct_mode),
+                     ("ct_smoothing", ct_smoothing), ("nu_ct_edge", nu_ct_edge)]:
         try:
             with np.errstate(all="ignore"):
                 ok = bool(fn())

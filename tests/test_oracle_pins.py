@@ -649,3 +649,109 @@ def face_velocity_case(oracle_mod, lib=None):
 
 def test_irregular_mesh_face_velocity_interpolation(oracle_mod):
     assert face_velocity_case(oracle_mod)
+
+
+# ---------------------------------------------------------------------------
+# constrained transport details (Sec. 2.4): closed forms of the linearised
+# magnetic operator.  A face pencil of b_y along x, advanced by B_x with the
+# limiter off (first-order corrector), is a linear recursion with constant
+# coefficients when the velocity is uniform, so a single Fourier mode keeps
+# its shape and is multiplied by an amplification factor G; and for a
+# uniform b_y the response to a small velocity mode is linear in the mode,
+# carrying the transfer function of the face-velocity smoothing.
+# ---------------------------------------------------------------------------
+
+def ct_upwind_mode_case(oracle_mod, lib=None):
+    """Uniform velocity V > 0 (every edge velocity positive), b_y = A sin(theta i
+    + phi), limiter off.  Upwind first-order predictor over half a step
+    (eq0363 with the upwind cell of eq0364), then the corrector flux of the
+    upwind predicted cell over a full step: with nu = V dt / h and
+    z = 1 - exp(-i theta) the mode is multiplied by G = 1 - nu z + nu^2 z^2 / 2
+    (the two-stage expansion of exp(-nu z)).  A downwind predictor gives
+    1 - nu z - nu^2 z (exp(i theta) - 1) / 2 instead.  True when every face
+    matches to 1e-14 of A."""
+    n, m, A, phase, V, nu = 32, 3, 0.7, 0.4, 1.3, 0.4
+    theta = 2 * np.pi * m / n
+    i = np.arange(n)
+    by = (A * np.sin(theta * i + phase))[None, None, :]
+    one = np.ones((1, 1, n))
+    st = W.assemble(one, (V * one, 0 * one, 0 * one), 1.0, (0 * one, by, 0 * one), 5 / 3, W.BC_PERIODIC)
+    h = 1.0 / n
+    ob = oracle_mod.OracleBox(n, 1, 1, 5 / 3, h=(h, 1.0, 1.0), limiter=2, lib=lib)
+    ob.set_state(st)
+    ob.ct(0, nu * h / V)
+    z = 1 - np.exp(-1j * theta)
+    G = 1 - nu * z + 0.5 * nu * nu * z * z
+    ref = A * np.imag(G * np.exp(1j * (theta * i + phase)))
+    return np.max(np.abs(ob.state[6, 0, 0] - ref)) <= 1e-14 * A
+
+
+def ct_smoothing_case(oracle_mod, lib=None):
+    """Uniform b_y = B, velocity V + eps sin(theta i) with eps << V (all edge
+    velocities positive), limiter off.  To first order in eps the change of
+    b_y is linear in the smoothed face velocity vh (eq0362), whose mode is
+    the velocity mode times the [1,2,1]/4 transfer function cos^2(theta/2);
+    with lambda = dt/h and z = 1 - exp(-i theta):
+      (b_new - B) / eps = -lambda B cos^2(theta/2) Im[(z - V lambda z^2 / 2) e^{i theta i}].
+    Without the smoothing the factor would be 1 (28 % off at this theta).
+    True when the response matches to 1e-4 of its largest value (the
+    remainder is of order eps)."""
+    n, m, B, V, eps = 32, 5, 0.8, 1.1, 1e-6
+    theta = 2 * np.pi * m / n
+    i = np.arange(n)
+    vx = (V + eps * np.sin(theta * i))[None, None, :]
+    one = np.ones((1, 1, n))
+    st = W.assemble(one, (vx, 0 * one, 0 * one), 1.0, (0 * one, B * one, 0 * one), 5 / 3, W.BC_PERIODIC)
+    h = 1.0 / n
+    lam = 0.45 / V
+    ob = oracle_mod.OracleBox(n, 1, 1, 5 / 3, h=(h, 1.0, 1.0), limiter=2, lib=lib)
+    ob.set_state(st)
+    ob.ct(0, lam * h)
+    got = (ob.state[6, 0, 0] - B) / eps
+    z = 1 - np.exp(-1j * theta)
+    ref = -lam * B * math.cos(theta / 2) ** 2 * np.imag((z - 0.5 * V * lam * z * z) * np.exp(1j * theta * i))
+    return np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
+
+
+def ct_edge_velocity_case(oracle_mod, lib=None):
+    """Irregular mesh along x (reading C-27): the edge velocity whose sign picks
+    the upwind cell is the linear interpolation of the two smoothed face
+    velocities to the interface, (w_b v_a + w_a v_b) / (w_a + w_b).  The cell
+    velocities are linear in the cell index (the [1,2,1] smoothing leaves
+    them unchanged away from the boundary) and change sign between cells 5
+    and 6: v_5 = -0.3 a, v_6 = 0.7 a.  With widths (w_5, w_6) = (1, 4) the
+    interpolated velocity at the interface is -0.1 a, so cell 6 is upwind;
+    with (4, 1) it is +0.5 a and cell 5 is upwind.  b_y is 1 in cell 5 and
+    0 elsewhere: when cell 6 is upwind of both its interfaces no flux reaches
+    it and its b_y stays exactly 0; when cell 5 is upwind of the shared
+    interface, b_y of cell 6 changes.  (Swapped weights, or the plain mean
+    of the uniform mesh, pick cell 5 in both cases.)"""
+    n, a, dt = 12, 0.1, 0.01
+    i = np.arange(n)
+    vx = (a * (i - 5.3))[None, None, :]
+    by = np.zeros((1, 1, n))
+    by[0, 0, 5] = 1.0
+    one = np.ones((1, 1, n))
+    st = W.assemble(one, (vx, 0 * one, 0 * one), 1.0, (0 * one, by, 0 * one), 5 / 3, W.BC_OUTFLOW)
+    out = []
+    for w5, w6 in ((1.0, 4.0), (4.0, 1.0)):
+        wx = np.full(n, 1.0 / n)
+        wx[5], wx[6] = w5 / n, w6 / n
+        ob = oracle_mod.OracleBox(n, 1, 1, 5 / 3, bc=W.BC_OUTFLOW, h=(1.0 / n, 1.0, 1.0), limiter=2, lib=lib,
+                                  widths=[wx, None, None])
+        ob.set_state(st)
+        ob.ct(0, dt)
+        out.append(ob.state[6, 0, 0, 6])
+    return out[0] == 0.0 and abs(out[1]) > 1e-4
+
+
+def test_ct_upwind_predictor_mode_amplification(oracle_mod):
+    assert ct_upwind_mode_case(oracle_mod)
+
+
+def test_ct_face_velocity_smoothing_transfer_function(oracle_mod):
+    assert ct_smoothing_case(oracle_mod)
+
+
+def test_irregular_mesh_ct_edge_velocity_interpolation(oracle_mod):
+    assert ct_edge_velocity_case(oracle_mod)

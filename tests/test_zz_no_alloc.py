@@ -4,8 +4,9 @@ device memory themselves, or loops where a cudaMalloc is not allowed).
 
 It is called through the C ABI on device-resident states and must give what
 fish_diagnostics gives for the same state, on consecutive calls that share
-its fixed scratch array -- including a call on a box with fewer z-planes
-than the one before, so that stale rows would show.  Tolerances: each total
+its fixed scratch array -- a box with as many z-planes as the array has
+rows, then boxes with fewer z-planes than the one before, so that stale
+rows would show.  Tolerances: each total
 to 1e-12 of the sum of |values| times the cell volume (the two entry points
 add in different orders), max |div b| to 1e-12 of max|b| / min(h).  Kept in
 a file of its own that runs last."""
@@ -57,8 +58,10 @@ def test_noalloc_diagnostics_match_existing_entry_point(F):
     import torch
     cases = [
         (W.random_smooth(24, 20, 18, seed=21, h=(0.04, 0.05, 0.055)), "fp64", 2),
+        # as many z-planes as the scratch array has rows
+        (W.random_smooth(4, 4, 4096, seed=24), "fp32", 1),
         (W.random_smooth(16, 12, 10, seed=22, bc=W.BC_OUTFLOW), "fp32", 3),
-        (W.random_smooth(16, 12, 10, seed=22, bc=W.BC_OUTFLOW), "fp32", 3),
+        (W.random_smooth(20, 16, 12, seed=23), "fp32", 2),
     ]
     stream = torch.cuda.current_stream()
     for w, prec, steps in cases:
