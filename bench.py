@@ -406,6 +406,9 @@ def run_fish(args, rank, world, local):
             from paper_0910_2854_gb300 import reports
             try:
                 batch = reports.batch()
+                peak_b, _ = measured_peak()
+                # the method's floor (384 B/cell per double step) at the batch's rate
+                batch["step_frac"] = 384 * batch["cells"] / (batch["ms_per_step"] * 1e-3) / 1e9 / peak_b
                 batch["workload"] = ("batch of 64 seeded boxes 32^3..160^3 (Sod / Brio-Wu / blast), FP32, one graph "
                                      "of persistent work-queue sweeps per double step, autotuned")
             except Exception as exc:  # report, do not hide

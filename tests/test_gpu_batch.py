@@ -133,3 +133,47 @@ def test_autotuner_picks_a_measured_choice(F, tmp_path, monkeypatch):
     again = autotune.tune([w.dims for w in ws], [w.gamma for w in ws], [w.bc for w in ws], [w.state for w in ws],
                           hs=[w.h for w in ws], candidates=cands)
     assert again == c  # served from the cache
+
+
+def test_bench_size_batch_parity(F):
+    """The 64 seeded boxes of the throughput batch (sizes 32..160 per axis,
+    Sod / Brio-Wu / blast), two double steps: every box against the
+    single-box FP32 path to 1e-6 (time steps and states), and the four
+    smallest tube boxes against the FP64 oracle to 1e-5.  (The batch's
+    blasts are centred: their mirror-symmetric stagnation edges carry edge
+    velocities that are zero only up to round-off, where FP32 may take the
+    other upwind cell than FP64 -- reading C-20 -- so the oracle comparison
+    takes tube boxes.)"""
+    specs = W.batch_specs()
+    ws = [W.batch_box(*s) for s in specs]
+    assert len(ws) == 64
+    b = make_batch(F, ws)
+    b.step(0.5, 2)
+    dts = b.last_dt()
+    for i, w in enumerate(ws):
+        box = F.Box(*w.dims, w.gamma, bc=w.bc, precision="fp32", h=w.h)
+        box.set_state(w.state)
+        box.step_cfl(0.5, 2)
+        assert abs(box.last_dt() - dts[i]) <= 1e-6 * dts[i], i
+        assert rel_err(b.get_state(i), box.get_state()) <= 1e-6, i
+        box.close()
+    b.close()
+
+    tubes = sorted((i for i, s in enumerate(specs) if s[0] != "blast"), key=lambda i: np.prod(ws[i].dims))[:4]
+    sel = [ws[i] for i in tubes]
+    b = make_batch(F, sel)
+    obs = []
+    for w in sel:
+        ob = oracle.OracleBox(*w.dims, w.gamma, bc=w.bc, h=w.h)
+        ob.set_state(w.state)
+        obs.append(ob)
+    for step in range(2):
+        b.step(0.5, 1)
+        d = b.last_dt()
+        for i, ob in enumerate(obs):
+            ref = ob.cfl(0.5)
+            assert abs(d[i] - ref) <= (1e-5 if step == 0 else 1e-4) * ref, (tubes[i], step)
+            ob.step(d[i])
+    for i, ob in enumerate(obs):
+        assert rel_err(b.get_state(i), ob.state) <= 1e-5, tubes[i]
+    b.close()
