@@ -267,9 +267,13 @@ def radial_profile(rho, h):
     return (np.arange(n + 1) + 0.5) * h, prof
 
 
-def validation(name, n=None, precision="fp32"):
+def validation(name, n=None, precision="fp32", cfl=None):
+    """Run one of the paper's validation problems to its end time at the
+    printed CFL number (or ``cfl``) and report value ranges."""
     from . import FISH_LIM_MINMOD, FISH_LIM_VANLEER
     gen, n0, k, lim = VALIDATION[name]
+    if cfl is not None:
+        k = float(cfl)
     n = int(n or n0)
     w = gen(n)
     t_end = w.meta["t_end"]
@@ -317,7 +321,8 @@ def main(argv):
     what = argv[1] if len(argv) > 1 else "batch"
     t0 = time.time()
     if what == "validation":
-        res = validation(argv[2], *(argv[3:4] or [None]), *(argv[4:5] or ["fp32"]))
+        res = validation(argv[2], *(argv[3:4] or [None]), *(argv[4:5] or ["fp32"]),
+                         *([float(argv[5])] if len(argv) > 5 else []))
         res["wall_s_total"] = time.time() - t0
         print(json.dumps(res), flush=True)
         return

