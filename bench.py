@@ -12,7 +12,10 @@ dominant kernel.
 N > 1 runs as one rank per GPU under torch.distributed.run; every rank
 advances its own box (independent replicas, no collective on the data
 path), so scaling is weak and the value is the cells of all ranks divided by
-the slowest rank's time.  ``--impl reference`` times the CPU oracle (the
+the slowest rank's time.  With --decomp the ranks instead share one box split
+into z-slabs (ghost planes exchanged before every operator, all-reduced CFL
+step; strong scaling, the value is the box's cells over the slowest rank's
+time).  ``--impl reference`` times the CPU oracle (the
 FP64 C implementation in oracle/) on a bounded sample of the same workload.
 """
 from __future__ import annotations
@@ -66,6 +69,9 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--decomp", action="store_true",
+                   help="one box split into z-slabs over the ranks (halo exchange, strong scaling) instead of one "
+                        "box per rank")
     p.add_argument("--no-same-box", action="store_true",
                    help="skip the FP64 run of the workload's own box (like-for-like FP32/FP64 ratio and L1(rho))")
     p.add_argument("--oracle-sample", type=float, default=None,
@@ -443,6 +449,82 @@ def run_fish(args, rank, world, local):
     return 0
 
 
+def run_fish_decomp(args, rank, world, local):
+    """One n^3 turbulence box split into z-slabs over the ranks (host-driven
+    operators with a ghost-plane exchange before each, no graph)."""
+    import torch
+    import paper_0910_2854_gb300 as F
+    from paper_0910_2854_gb300 import decomp
+    from paper_0910_2854_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    n = args.n or WORKLOAD["n"]
+    k0, nk, lo, hi = decomp.slab_extent(n, rank, world, True)
+    w = W.turbulence(n, device="cuda", dtype=torch.float32)
+    idx = torch.arange(k0 - lo, k0 + nk + hi, device="cuda") % n
+    slab = w.state.view(8, n, n, n).index_select(1, idx).contiguous()
+    gamma, h = w.gamma, w.h
+    del w
+    torch.cuda.empty_cache()
+    box = F.Box(n, n, lo + nk + hi, gamma, precision="fp32", h=h)
+    box.set_state(slab)
+    del slab
+    torch.cuda.empty_cache()
+    run = decomp.SlabRun(box, n, n, n, rank, world, periodic=True, dist=dist, device="cuda", dtype=torch.float32)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    run.step_cfl(CFL, args.warmup)
+    barrier()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = box.launch_count()
+    e0.record(box.stream)
+    run.step_cfl(CFL, args.steps)
+    e1.record(box.stream)
+    e1.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = box.launch_count() - l0
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = n ** 3 / (ms_step * 1e-3)
+    box.close()
+    if rank == 0:
+        peak, peak_kind = measured_peak()
+        per_gpu = 384 * n ** 3 / world / (ms_step * 1e-3) / 1e9
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded, generated on the device)",
+                "config": {"workload": WORKLOAD["workload"], "cells": n ** 3, "cfl": CFL,
+                           "parallelism": "z-slabs x%d (%d ghost planes exchanged before every operator, "
+                                          "all-reduced CFL step)" % (world, decomp.HALO),
+                           "l2": "inputs larger than L2"},
+                "roofline": {"bound": "hbm", "achieved": per_gpu, "peak": peak, "unit": "GB/s",
+                             "frac": per_gpu / peak, "traffic": None,
+                             "kernel": "whole double step per GPU (384 B/cell floor)", "peak_source": peak_kind},
+                "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": clk,
+                "exchanges_per_step": run.exchanges / (args.steps + args.warmup)}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.oracle_sample is not None:
@@ -452,6 +534,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.decomp:
+        return run_fish_decomp(args, rank, world, local)
     return run_fish(args, rank, world, local)
 
 

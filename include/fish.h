@@ -147,6 +147,12 @@ int fish_set_mesh(fish_ctx *ctx, const double *dx, const double *dy, const doubl
  * (eq0083-eq0084, reading C-15) for the current state.  Synchronises. */
 int fish_cfl_dt(fish_ctx *ctx, double k, double *dt_out);
 
+/* The same over the z-planes k0 .. k0+nk-1 only (a z-slab of a box split
+ * over several GPUs, whose ghost planes stay out of the minimum; the slab's
+ * time step is then the minimum over all slabs).  FISH_ERR_ARG for a range
+ * outside [0, nz). */
+int fish_cfl_dt_planes(fish_ctx *ctx, double k, int k0, int nk, double *dt_out);
+
 /* One full double step u^{n+2} = L_fwd L_bwd u^n (eq0081-eq0082, reading
  * C-4): L_x B_x L_y B_y L_z B_z B_z L_z B_y L_y B_x L_x, every operator with
  * the full dt, so time advances by 2*dt.  Asynchronous. */
@@ -176,6 +182,19 @@ int fish_get_state_host(fish_ctx *ctx, void *state, int dtype);
 /* Copy the state into a device buffer of dtype FISH_F64 / FISH_F32.  Queued
  * on the stream; returns pending device errors only after fish_sync. */
 int fish_get_state_device(fish_ctx *ctx, void *state, int dtype);
+
+/* Copy the z-planes k0 .. k0+nk-1 of all 8 fields to (get) or from (set) a
+ * buffer of 8*nk*nx*ny values in the context's precision, field after field,
+ * each field's nk planes contiguous, every plane in the context's current
+ * memory layout (x fastest, or y fastest while an x sweep pair is active; a
+ * z-plane is contiguous in both).  The buffer may be host or device memory
+ * (pinned host memory for full bandwidth).  Queued on the stream; the
+ * caller synchronises before reading or reusing the buffer.  Used to
+ * exchange ghost slabs between the z-slabs of a box split over several
+ * GPUs (the paper's cuboid decomposition, Sec. 3).  FISH_ERR_ARG for a range
+ * outside [0, nz) or a NULL buffer. */
+int fish_get_planes(fish_ctx *ctx, int k0, int nk, void *dst);
+int fish_set_planes(fish_ctx *ctx, int k0, int nk, const void *src);
 
 /* out[0..7] = volume-weighted totals of the 8 fields (FP64 accumulation in a
  * fixed order); out[8] = max |div b| (eq0341) over cells whose six faces are

@@ -116,6 +116,8 @@ def _bind(lib):
     lib.oracle_step.restype = ctypes.c_int
     lib.oracle_cfl.argtypes = [P, D, ctypes.c_double]
     lib.oracle_cfl.restype = ctypes.c_double
+    lib.oracle_cfl_planes.argtypes = [P, D, ctypes.c_double, ctypes.c_long, ctypes.c_long]
+    lib.oracle_cfl_planes.restype = ctypes.c_double
     lib.oracle_diag.argtypes = [P, D, D]
     lib.oracle_diag.restype = None
     return lib
@@ -235,6 +237,11 @@ class OracleBox:
     def cfl(self, k):
         p = self._problem()
         return float(self._L().oracle_cfl(ctypes.byref(p), self._ptr(), float(k)))
+
+    def cfl_planes(self, k, k0, nk):
+        """The CFL step with the minimum over the z-planes k0 .. k0+nk-1."""
+        p = self._problem()
+        return float(self._L().oracle_cfl_planes(ctypes.byref(p), self._ptr(), float(k), int(k0), int(nk)))
 
     def diag(self):
         """8 volume-weighted field totals and max |div b|."""

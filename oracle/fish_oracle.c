@@ -764,15 +764,18 @@ int oracle_step(const or_problem *P, double *state, double dt, int nsteps)
 /* CFL time step (eq0083-eq0084, reading C-15):
  *   dt = k * min over cells and d of h_d / (|v_d| + c_F,d),
  * c_F,d the fast speed along d with the cell-centred field. */
-double oracle_cfl(const or_problem *P, const double *state, double k)
+/* eq0083-eq0084 with the minimum taken over the z-planes k0 .. k0+nk-1 only
+ * (cells of other planes still serve as lower neighbours for the
+ * cell-centred field). */
+double oracle_cfl_planes(const or_problem *P, const double *state, double k, long k0, long nk)
 {
-    const long N = (long)P->n[0] * P->n[1] * P->n[2];
+    const long plane = (long)P->n[0] * P->n[1];
     double *q[8];
     double best = INFINITY;
     long idx;
     or_fields(P, (double *)state, q);
 #pragma omp parallel for reduction(min : best) schedule(static)
-    for (idx = 0; idx < N; ++idx) {
+    for (idx = k0 * plane; idx < (k0 + nk) * plane; ++idx) {
         long i = idx % P->n[0], j = (idx / P->n[0]) % P->n[1], kk = idx / ((long)P->n[0] * P->n[1]);
         double bcc[3];
         int ax, d, fl = 0;
@@ -794,6 +797,11 @@ double oracle_cfl(const or_problem *P, const double *state, double k)
         }
     }
     return k * best;
+}
+
+double oracle_cfl(const or_problem *P, const double *state, double k)
+{
+    return oracle_cfl_planes(P, state, k, 0, P->n[2]);
 }
 
 /* Diagnostics: out[0..7] = sum over cells of each field times the cell

@@ -34,7 +34,7 @@ FISH_BATCH_OPT_LIMITER, FISH_BATCH_OPT_ORDER, FISH_BATCH_OPT_GROUPS, FISH_BATCH_
 # every symbol include/fish.h declares (checked by the CPU test suite)
 EXPORTS = ("fish_create", "fish_set_option", "fish_set_stream", "fish_set_allocator", "fish_set_state",
            "fish_set_state_device", "fish_set_state_host", "fish_set_potential", "fish_set_mesh", "fish_cfl_dt", "fish_step", "fish_step_cfl",
-           "fish_last_dt", "fish_apply", "fish_get_state", "fish_get_state_host", "fish_get_state_device", "fish_diagnostics",
+           "fish_last_dt", "fish_apply", "fish_get_state", "fish_get_state_host", "fish_get_state_device", "fish_get_planes", "fish_set_planes", "fish_cfl_dt_planes", "fish_diagnostics",
            "fish_sync", "fish_clear_error", "fish_last_error", "fish_launch_count", "fish_destroy",
            "fish_diagnostics_noalloc", "fish_probe_fp64_fma", "fish_batch_create", "fish_batch_set_option", "fish_batch_set_stream",
            "fish_batch_set_state", "fish_batch_step", "fish_batch_get_state", "fish_batch_last_dt",
@@ -85,6 +85,9 @@ def load(path: str = LIB_PATH):
             "fish_get_state": ([P, D], ctypes.c_int),
             "fish_get_state_device": ([P, P, ctypes.c_int], ctypes.c_int),
             "fish_get_state_host": ([P, P, ctypes.c_int], ctypes.c_int),
+            "fish_get_planes": ([P, ctypes.c_int, ctypes.c_int, P], ctypes.c_int),
+            "fish_cfl_dt_planes": ([P, ctypes.c_double, ctypes.c_int, ctypes.c_int, D], ctypes.c_int),
+            "fish_set_planes": ([P, ctypes.c_int, ctypes.c_int, P], ctypes.c_int),
             "fish_diagnostics": ([P, D], ctypes.c_int),
             "fish_sync": ([P], ctypes.c_int),
             "fish_clear_error": ([P], ctypes.c_int),
@@ -281,6 +284,13 @@ class Box:
         self._check(self._lib.fish_cfl_dt(self.ctx, float(k), ctypes.byref(out)), "fish_cfl_dt")
         return out.value
 
+    def cfl_dt_planes(self, k, k0, nk):
+        """CFL time step over the z-planes k0 .. k0+nk-1 only."""
+        out = ctypes.c_double()
+        self._check(self._lib.fish_cfl_dt_planes(self.ctx, float(k), int(k0), int(nk), ctypes.byref(out)),
+                    "fish_cfl_dt_planes")
+        return out.value
+
     def step(self, dt, nsteps=1):
         for _ in range(int(nsteps)):
             self._check(self._lib.fish_step(self.ctx, float(dt)), "fish_step")
@@ -323,6 +333,19 @@ class Box:
             raise ValueError("state has %d values, expected %d" % (size, 8 * np.prod(self.n)))
         self._check(self._lib.fish_get_state_host(self.ctx, ctypes.c_void_p(ptr), dt), "fish_get_state_host")
         return out
+
+    def get_planes(self, k0, nk, out):
+        """z-planes k0 .. k0+nk-1 of the 8 fields into ``out`` (a contiguous
+        torch tensor of 8*nk*nx*ny values of the box's precision, on the
+        device or in host memory); queued on the box's stream."""
+        self._check(self._lib.fish_get_planes(self.ctx, int(k0), int(nk), ctypes.c_void_p(out.data_ptr())),
+                    "fish_get_planes")
+        return out
+
+    def set_planes(self, k0, nk, src):
+        """The inverse of get_planes: overwrite z-planes k0 .. k0+nk-1."""
+        self._check(self._lib.fish_set_planes(self.ctx, int(k0), int(nk), ctypes.c_void_p(src.data_ptr())),
+                    "fish_set_planes")
 
     def get_state_device(self, out):
         import torch

@@ -357,27 +357,30 @@ int queue_sweeps(fish_ctx *c, bool fuse_cfl = false)
     return FISH_OK;
 }
 
-template <class T> int queue_cfl(fish_ctx *c)
+template <class T> int queue_cfl(fish_ctx *c, int k0 = 0, int nk = -1)
 {
     const T *in[8];
     for (int f = 0; f < 8; ++f) in[f] = (const T *)field_ptr(c, f);
-    FISH_CK(c, Launch<T>::cfl(in, geom(c), c->h, c->gamma, c->minbits, c->flags, c->stream, mesh_of<T>(c).get()),
+    FISH_CK(c,
+            Launch<T>::cfl(in, geom(c), c->h, c->gamma, c->minbits, c->flags, c->stream, mesh_of<T>(c).get(), k0,
+                           nk),
             "cfl launch");
     c->launches += 1;
     return FISH_OK;
 }
 
-// Standalone CFL reduction into minbits (reset first).
-int queue_cfl_min(fish_ctx *c)
+// Standalone CFL reduction into minbits (reset first), over the z-planes
+// k0 .. k0+nk-1 (nk < 0: all).
+int queue_cfl_min(fish_ctx *c, int k0 = 0, int nk = -1)
 {
     FISH_CK(c, fish::launch_reset_min(c->minbits, c->stream), "cfl reset launch");
     c->launches += 1;
-    return c->prec == FISH_PREC_FP64 ? queue_cfl<double>(c) : queue_cfl<float>(c);
+    return c->prec == FISH_PREC_FP64 ? queue_cfl<double>(c, k0, nk) : queue_cfl<float>(c, k0, nk);
 }
 
-int queue_cfl_dt(fish_ctx *c, double k, double *dt_target, double *dt_copy)
+int queue_cfl_dt(fish_ctx *c, double k, double *dt_target, double *dt_copy, int k0 = 0, int nk = -1)
 {
-    int r = queue_cfl_min(c);
+    int r = queue_cfl_min(c, k0, nk);
     if (r) return r;
     FISH_CK(c, fish::launch_cfl_finish(c->minbits, k, dt_target, dt_copy, c->stream), "cfl finish launch");
     c->launches += 1;
@@ -697,6 +700,18 @@ int fish_cfl_dt(fish_ctx *c, double k, double *dt_out)
     return check_flags(c);
 }
 
+int fish_cfl_dt_planes(fish_ctx *c, double k, int k0, int nk, double *dt_out)
+{
+    int r = ready(c);
+    if (r) return r;
+    c->cfl_pending = false;
+    if (!dt_out || !(k > 0.0) || k0 < 0 || nk < 1 || k0 + nk > c->n[2])
+        return fail(c, FISH_ERR_ARG, "bad CFL arguments");
+    if ((r = queue_cfl_dt(c, k, c->partial, nullptr, k0, nk))) return r;
+    FISH_CK(c, cudaMemcpyAsync(dt_out, c->partial, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "dt");
+    return check_flags(c);
+}
+
 int fish_step(fish_ctx *c, double dt)
 {
     int r = ready(c);
@@ -887,6 +902,45 @@ int fish_get_state_device(fish_ctx *c, void *state, int dtype)
         }
         c->launches += 1;
     }
+    return FISH_OK;
+}
+
+// z-planes [k0, k0+nk) of all 8 fields to / from a buffer laid out field
+// by field, each field's planes contiguous (a z-plane is contiguous in both
+// memory layouts: z is the slowest axis); the values stay in the context's
+// precision and current layout.
+int planes_check(fish_ctx *c, int k0, int nk, const void *buf)
+{
+    int r = ready(c);
+    if (r) return r;
+    if (!buf || nk < 0 || k0 < 0 || k0 + nk > c->n[2]) return fail(c, FISH_ERR_ARG, "bad plane range");
+    return FISH_OK;
+}
+
+int fish_get_planes(fish_ctx *c, int k0, int nk, void *dst)
+{
+    int r = planes_check(c, k0, nk, dst);
+    if (r) return r;
+    const size_t es = esize(c), plane = (size_t)c->n[0] * c->n[1];
+    for (int f = 0; f < 8; ++f)
+        FISH_CK(c, cudaMemcpyAsync((char *)dst + (size_t)f * nk * plane * es,
+                                   (const char *)field_ptr(c, f) + (size_t)k0 * plane * es, (size_t)nk * plane * es,
+                                   cudaMemcpyDefault, c->stream),
+                "plane copy");
+    return FISH_OK;
+}
+
+int fish_set_planes(fish_ctx *c, int k0, int nk, const void *src)
+{
+    int r = planes_check(c, k0, nk, src);
+    if (r) return r;
+    const size_t es = esize(c), plane = (size_t)c->n[0] * c->n[1];
+    for (int f = 0; f < 8; ++f)
+        FISH_CK(c, cudaMemcpyAsync((char *)field_ptr(c, f) + (size_t)k0 * plane * es,
+                                   (const char *)src + (size_t)f * nk * plane * es, (size_t)nk * plane * es,
+                                   cudaMemcpyDefault, c->stream),
+                "plane copy");
+    c->cfl_pending = false;  // the state changed outside a graph replay
     return FISH_OK;
 }
 

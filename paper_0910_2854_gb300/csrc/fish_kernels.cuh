@@ -37,6 +37,7 @@ template <class T> struct CFLArgs {
     unsigned long long *minbits;  // order-preserving bits of the positive minimum (double)
     unsigned *flags;
     const T *w[3] = {nullptr, nullptr, nullptr};  // irregular mesh: cell widths per axis (eq0420)
+    int k0 = 0, nk = -1;  // z-planes k0 .. k0+nk-1 only (nk < 0: all)
 };
 
 // FP32 signal speeds along the three axes of one cell, sharing the
@@ -77,14 +78,15 @@ __global__ void __launch_bounds__(256) cfl_kernel(CFLArgs<T> A)
     const Geom &g = A.g;
     const int f0 = g.ord[0], f1 = g.ord[1], f2 = g.ord[2];
     const int nf = g.n[f0], nm = g.n[f1], ns = g.n[f2];
-    const long long rows = (long long)nm * ns;
+    const int kb = A.nk < 0 ? 0 : A.k0;
+    const long long rows = (long long)nm * (A.nk < 0 ? ns : A.nk);
     double best = 1e300;   // min of h_d / (|v_d| + c_F,d)
     float fbest = 0.0f;    // FP32 path: max of (|v_d| + c_F,d) / h_d
     unsigned flags = 0;
     float rh[3];
     for (int d = 0; d < 3; ++d) rh[d] = (float)(1.0 / A.h[d]);
     for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
-        const int m = (int)(row % nm), k = (int)(row / nm);
+        const int m = (int)(row % nm), k = kb + (int)(row / nm);
         const long long rbase = (long long)m * g.st[f1] + (long long)k * g.st[f2];
         const long long om = (long long)(gmap(m - 1, nm, g.bc) - m) * g.st[f1];
         const long long ok = (long long)(gmap(k - 1, ns, g.bc) - k) * g.st[f2];

@@ -174,9 +174,12 @@ cudaError_t Launch<T>::ct(const T *rho, const T *md, const T *const b[3], T *con
 
 template <class T>
 cudaError_t Launch<T>::cfl(const T *const in[8], const Geom &g, const double h[3], double gamma,
-                           unsigned long long *minbits, unsigned *flags, cudaStream_t s, const T *const *w3)
+                           unsigned long long *minbits, unsigned *flags, cudaStream_t s, const T *const *w3,
+                           int k0, int nk)
 {
     CFLArgs<T> A;
+    A.k0 = k0;
+    A.nk = nk;
     if (w3)
         for (int a = 0; a < 3; ++a) A.w[a] = w3[a];
     for (int f = 0; f < 8; ++f) A.in[f] = in[f];
@@ -187,8 +190,8 @@ cudaError_t Launch<T>::cfl(const T *const in[8], const Geom &g, const double h[3
     A.minbits = minbits;
     A.flags = flags;
     // one block per row of the fastest axis, at most 8 resident blocks per SM
-    const long long rows = (long long)g.n[g.ord[1]] * g.n[g.ord[2]];
-    const unsigned grid = (unsigned)(rows < 152ll * 8 ? rows : 152ll * 8);
+    const long long rows = (long long)g.n[g.ord[1]] * (nk < 0 ? g.n[g.ord[2]] : nk);
+    const unsigned grid = (unsigned)(rows < 1 ? 1 : (rows < 152ll * 8 ? rows : 152ll * 8));
     cfl_kernel<T><<<grid, 256, 0, s>>>(A);
     return cudaGetLastError();
 }

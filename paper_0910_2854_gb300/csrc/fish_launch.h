@@ -26,9 +26,10 @@ template <class T> struct Launch {
                           const double *dt, const Geom &g, int d, int lim, const double h[3],
                           unsigned *flags, cudaStream_t s, const T *const *w3 = nullptr);
     // CFL minimum into *minbits (order-preserving bits of a positive double).
+    // k0, nk: only the z-planes k0 .. k0+nk-1 (nk < 0: all)
     static cudaError_t cfl(const T *const in[8], const Geom &g, const double h[3], double gamma,
                            unsigned long long *minbits, unsigned *flags, cudaStream_t s,
-                           const T *const *w3 = nullptr);
+                           const T *const *w3 = nullptr, int k0 = 0, int nk = -1);
     // Per-block FP64 partial totals and max |div b| into partial[nblocks][9].
     static cudaError_t diag(const T *const in[8], const Geom &g, const double h[3], double *partial,
                             int nblocks, cudaStream_t s, const T *const *w3 = nullptr);

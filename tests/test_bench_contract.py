@@ -44,3 +44,13 @@ def test_gpu_arm_line():
     # a full round trip per step: the whole FP32 state up and down
     assert e["value"] > 0 and e["h2d_bytes_per_step"] == 32 * 128 ** 3 and e["d2h_bytes_per_step"] == 32 * 128 ** 3
     assert {"sm_mhz", "sm_max_mhz", "reasons"} <= set(d["clocks"])
+
+
+@pytest.mark.gpu
+def test_gpu_decomposed_line():
+    """--decomp on one GPU: the z-slab path with the rank exchanging ghost
+    planes with itself (periodic), strong scaling."""
+    d = run_bench("--decomp", "--n", "128", "--steps", "1", "--warmup", "3")
+    assert {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "scaling"} <= set(d)
+    assert d["scaling"] == "strong" and d["value"] > 0 and d["gpu_launches"] > 0
+    assert d["exchanges_per_step"] == 13
