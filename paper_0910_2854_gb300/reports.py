@@ -1,10 +1,11 @@
 """Measurements of the GPU path beyond the throughput line of bench.py, run
 on one GPU and printed as one JSON line each:
 
-  python -m paper_0910_2854_gb300.reports polytrope [n] [steps]
+  python -m paper_0910_2854_gb300.reports polytrope [n] [tau_units]
       n = 1 polytrope (n^3, FP32 with the hydrostatic island) with and
-      without the hydrostatic-gradient correction: central density drift
-      and largest spurious velocity after `steps` double steps.
+      without the hydrostatic-gradient correction for tau_units hydrostatic
+      times (default 20, as in the paper): time series of the central
+      density and of the largest spurious speed inside the star.
   python -m paper_0910_2854_gb300.reports fp32_vs_fp64 [n] [steps]
       random-phase turbulence n^3: FP32 and FP64 paths each advanced with
       their own CFL steps; L1 density difference relative to the FP64 path,
@@ -19,7 +20,7 @@ on one GPU and printed as one JSON line each:
       the FP64 path on the Orszag-Tang box n^3: one double step and each
       operator timed with CUDA events, next to the probed FP64 FMA rate of
       the device.
-  python -m paper_0910_2854_gb300.reports validation <name> [n] [fp32|fp64]
+  python -m paper_0910_2854_gb300.reports validation <name> [n] [fp32|fp64] [cfl]
       one of the paper's validation problems (sedov, spherical_riemann,
       magnetic_explosion, rotor, mhd_riemann_2d) at the paper's size (or n)
       run to the paper's end time: value ranges against the printed ones,
@@ -32,6 +33,7 @@ seeded synthetic fields of ``workloads``.
 from __future__ import annotations
 
 import json
+import math
 import sys
 import time
 
@@ -52,29 +54,49 @@ def _timed_steps(box, torch, k, steps):
     return e0.elapsed_time(e1)
 
 
-def polytrope(n=384, steps=1000, k=0.5):
+def polytrope(n=384, tau_units=20.0, k=0.5, samples=40):
+    """The n = 1 polytrope in its fixed potential (FP32, unsplit gravity),
+    with and without the hydrostatic-gradient correction, for tau_units
+    hydrostatic times tau_HSE = (rho_mean G)^(-1/2) / 2 (the paper's Sec. 4
+    runs 20).  Records, about ``samples`` times, the central density (mean
+    of the 8 cells around the centre of an even box, else the central cell)
+    normalised to its initial value and the largest speed inside the star."""
     import torch
     w = W.polytrope(n)
+    R, rho_c, G = 1.0, 1.0, 1.0
+    M = 4.0 * R ** 3 * rho_c / math.pi
+    rho_mean = M / (4.0 / 3.0 * math.pi * R ** 3)
+    tau = 0.5 / math.sqrt(rho_mean * G)
+    t_end = tau_units * tau
     c = n // 2
-    out = {"report": "polytrope", "n": n, "steps": steps, "cfl": k, "precision": "fp32",
-           "rho_c0": float(w.state[0, c, c, c])}
+    sl = slice(c - 1, c + 1) if n % 2 == 0 else slice(c, c + 1)
+
+    def central(st):
+        return float(st[0, sl, sl, sl].mean())
+
+    out = {"report": "polytrope", "n": n, "cfl": k, "precision": "fp32", "tau_hse": tau, "t_end": t_end,
+           "rho_c0": central(w.state)}
+    inside = w.state[0] > 10 * w.state[0].min()
     for hse in (False, True):
         box = Box(*w.dims, w.gamma, bc=w.bc, precision="fp32", h=w.h, hse=hse)
         box.set_state(w.state)
         box.set_potential(w.phi)
-        t = 0.0
-        ms = 0.0
-        for _ in range(steps // 50):
-            ms += _timed_steps(box, torch, k, 50)
-            t += 2 * 50 * box.last_dt()  # approximate: the last dt of each chunk
-        st = box.get_state()
-        v = np.sqrt(st[1] ** 2 + st[2] ** 2 + st[3] ** 2) / st[0]
-        inside = w.state[0] > 10 * w.state[0].min()
+        t, steps, ms = 0.0, 0, 0.0
+        series = [(0.0, 1.0, 0.0)]
+        next_sample = t_end / samples
+        while t < t_end:
+            ms += _timed_steps(box, torch, k, 1)
+            t += 2.0 * box.last_dt()
+            steps += 1
+            if t >= next_sample or t >= t_end:
+                st = box.get_state()
+                v = np.sqrt(st[1] ** 2 + st[2] ** 2 + st[3] ** 2) / st[0]
+                series.append((t / tau, central(st) / out["rho_c0"], float(v[inside].max())))
+                next_sample += t_end / samples
         key = "hse" if hse else "no_hse"
-        out[key] = {"rho_c": float(st[0, c, c, c]),
-                    "rho_c_drift": float(st[0, c, c, c] / out["rho_c0"] - 1.0),
-                    "vmax_star": float(v[inside].max()), "vmax": float(v.max()),
-                    "ms_per_step": ms / steps, "t_approx": t}
+        out[key] = {"double_steps": steps, "ms_per_step": ms / steps,
+                    "rho_c_drift_end": series[-1][1] - 1.0, "vmax_star_end": series[-1][2],
+                    "series_t_over_tau_rho_c_vmax": series}
         box.close()
         torch.cuda.empty_cache()
     return out
