@@ -251,6 +251,61 @@ template <class T> struct TransArgs {
 #define FISH_TR_ROWS 64
 #endif
 // tile height: FP64 tiles stay within the 48 KB of static shared memory
+// FP32 transpose with 16-byte accesses: tiles of 64 x 64 elements, each
+// thread moves four float4 of a field per tile (source rows of 256 bytes
+// read whole, destination rows of 256 bytes written whole), the next
+// field's float4 loads in flight while the current tile is stored.  Needs
+// nr and nc multiples of 4 (16-byte aligned rows).  Grid: ceil(nr/64) x
+// ceil(nc/64) x nz, 256 threads.
+template <class T>
+__global__ void __launch_bounds__(256) transpose4_kernel(TransArgs<T> A)
+{
+    static_assert(sizeof(T) == 4, "16-byte accesses of four 4-byte elements");
+    __shared__ T tile[2][64][65];
+    const int r0 = blockIdx.x * 64, c0 = blockIdx.y * 64;
+    const long long zoff = (long long)blockIdx.z * A.plane;
+    const int t = threadIdx.x;
+    const int lr = t >> 4, l4 = (t & 15) * 4;  // row within a 16-row band, first element of the float4
+    float4 v[4];
+    auto load = [&](const T *src) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = c0 + lr + 16 * k, r = r0 + l4;
+            v[k] = (c < A.nc && r < A.nr) ? __ldg(reinterpret_cast<const float4 *>(src + zoff + (long long)c * A.nr + r))
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    load(A.src[0]);
+#pragma unroll 1
+    for (int f = 0; f < A.nf; ++f) {
+        const int b = f & 1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            T *row = &tile[b][lr + 16 * k][l4];
+            row[0] = v[k].x;
+            row[1] = v[k].y;
+            row[2] = v[k].z;
+            row[3] = v[k].w;
+        }
+        __syncthreads();
+        if (f + 1 < A.nf) load(A.src[f + 1]);
+        T *__restrict__ dst = A.dst[f] + zoff;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            // destination row r0 + lr + 16k holds source column r0 + lr + 16k
+            const int rl = lr + 16 * k, r = r0 + rl, c = c0 + l4;
+            if (r < A.nr && c < A.nc) {
+                float4 o;
+                o.x = tile[b][l4 + 0][rl];
+                o.y = tile[b][l4 + 1][rl];
+                o.z = tile[b][l4 + 2][rl];
+                o.w = tile[b][l4 + 3][rl];
+                *reinterpret_cast<float4 *>(dst + (long long)r * A.nc + c) = o;
+            }
+        }
+    }
+}
+
 template <class T> constexpr int tr_rows() { return sizeof(T) == 8 && FISH_TR_ROWS > 64 ? 64 : FISH_TR_ROWS; }
 template <class T>
 __global__ void __launch_bounds__(256) transpose_kernel(TransArgs<T> A)

@@ -224,6 +224,18 @@ cudaError_t Launch<T>::transpose(const T *const src[8], T *const dst[8], int nf,
     A.nr = nr;
     A.nc = nc;
     A.plane = (long long)nr * nc;
+#ifndef FISH_TR_SCALAR
+    if constexpr (sizeof(T) == 4) {
+        // 16-byte accesses where every row starts 16-byte aligned
+        bool al = nr % 4 == 0 && nc % 4 == 0;
+        for (int f = 0; f < nf; ++f) al = al && ((uintptr_t)src[f] & 15) == 0 && ((uintptr_t)dst[f] & 15) == 0;
+        if (al) {
+            dim3 grid4((nr + 63) / 64, (nc + 63) / 64, nz);
+            transpose4_kernel<T><<<grid4, 256, 0, s>>>(A);
+            return cudaGetLastError();
+        }
+    }
+#endif
     dim3 grid((nr + 31) / 32, (nc + tr_rows<T>() - 1) / tr_rows<T>(), nz);
     transpose_kernel<T><<<grid, dim3(32, 8), 0, s>>>(A);
     return cudaGetLastError();
