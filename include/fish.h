@@ -230,7 +230,8 @@ int fish_probe_fp64_fma(double *fma_per_s);
  * eq0084 with the operators of Sec. 2): its result equals that of a fish_ctx
  * of the same box stepped with fish_step_cfl.  The state layout of a box is
  * the one above.  Every box needs even nx and ny (the x and y columns are
- * advanced in pairs). */
+ * advanced in pairs); all boxes together hold at most 2^31 - 2^20 cells
+ * (FISH_ERR_ARG beyond). */
 typedef struct fish_batch fish_batch;
 
 /* batch option keys (fish_batch_set_option) */

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(128, FISH_COL_MINB)
         Ab.rh[1] = B.rh[1];
         Ab.rh[2] = B.rh[2];
         for (int g = 0; g < I.groups; ++g)
-            fluid_columns<P2, false, false, LIM, true, CFLF>(Ab, (long long)I.first + 128ll * g + threadIdx.x);
+            fluid_columns<P2, false, false, LIM, true, CFLF, false, int>(Ab, (long long)I.first + 128ll * g + threadIdx.x);
     }
 }
 
@@ -175,6 +175,73 @@ __global__ void __launch_bounds__(256) transpose_batch_kernel(const float *const
     }
 }
 
+// The same with 16-byte accesses on 64 x 64 tiles (the single-box FP32
+// transpose's scheme: four float4 per thread and field, the next field's
+// loads in flight); every box needs nr, nc and its offset multiples of 4.
+__global__ void __launch_bounds__(256) transpose4_batch_kernel(const float *const *src, float *const *dst,
+                                                               const BatchTile *__restrict__ tiles, int nbox)
+{
+    __shared__ float tile[2][64][65];
+    __shared__ int s_box;
+    const long long bid = blockIdx.x + (long long)gridDim.x * blockIdx.y;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = nbox - 1;
+        while (lo < hi) {  // last box whose first block <= bid
+            const int mid = (lo + hi + 1) >> 1;
+            if (tiles[mid].first <= bid) lo = mid;
+            else hi = mid - 1;
+        }
+        s_box = lo;
+    }
+    __syncthreads();
+    const BatchTile T = tiles[s_box];
+    const long long tb = bid - T.first;
+    if (tb >= (long long)T.tr * T.tc * T.nz) return;  // whole block
+    const int z = (int)(tb / ((long long)T.tr * T.tc));
+    const int rem = (int)(tb - (long long)z * T.tr * T.tc);
+    const int r0 = (rem % T.tr) * 64, c0 = (rem / T.tr) * 64;
+    const long long zoff = T.off + (long long)z * T.nr * T.nc;
+    const int t = threadIdx.x;
+    const int lr = t >> 4, l4 = (t & 15) * 4;
+    float4 v[4];
+    auto load = [&](const float *sp) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int c = c0 + lr + 16 * k, r = r0 + l4;
+            v[k] = (c < T.nc && r < T.nr) ? __ldg(reinterpret_cast<const float4 *>(sp + zoff + (long long)c * T.nr + r))
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    load(src[0]);
+#pragma unroll 1
+    for (int f = 0; f < 8; ++f) {
+        const int b = f & 1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float *row = &tile[b][lr + 16 * k][l4];
+            row[0] = v[k].x;
+            row[1] = v[k].y;
+            row[2] = v[k].z;
+            row[3] = v[k].w;
+        }
+        __syncthreads();
+        if (f + 1 < 8) load(src[f + 1]);
+        float *__restrict__ dp = dst[f] + zoff;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int rl = lr + 16 * k, r = r0 + rl, c = c0 + l4;
+            if (r < T.nr && c < T.nc) {
+                float4 o;
+                o.x = tile[b][l4 + 0][rl];
+                o.y = tile[b][l4 + 1][rl];
+                o.z = tile[b][l4 + 2][rl];
+                o.w = tile[b][l4 + 3][rl];
+                *reinterpret_cast<float4 *>(dp + (long long)r * T.nc + c) = o;
+            }
+        }
+    }
+}
+
 // dt[b] = k * min[b] for every box; resets the minima
 __global__ void batch_finish_kernel(unsigned long long *minbits, int nbox, double k, double *dt, double *dt_last)
 {
@@ -225,8 +292,11 @@ struct fish_batch {
     BatchBox *boxes[3] = {};      // per sweep direction
     BatchItem *fitems[3] = {}, *citems[3] = {};
     int nfitems[3] = {0, 0, 0}, ncitems[3] = {0, 0, 0};
-    BatchTile *ttiles[2] = {};    // layout 0 -> 1 and 1 -> 0
+    BatchTile *ttiles[2] = {};    // layout 0 -> 1 and 1 -> 0 (32 x 32 tiles)
     long long ttotal[2] = {0, 0};
+    BatchTile *ttiles4[2] = {};   // the same in 64 x 64 tiles (16-byte accesses)
+    long long ttotal4[2] = {0, 0};
+    bool t4 = false;              // every box allows the 16-byte transpose
     const float **tsrc = nullptr;  // device tables: per buffer parity, 8 source then 8 destination field pointers
     std::vector<void *> owned;
     bool tables = false;
@@ -393,6 +463,26 @@ int build_tables(fish_batch *b)
             return bfail(b, FISH_ERR_OOM, "batch table allocation failed");
         FISH_BCK(b, cudaMemcpy(b->ttiles[L], tt.data(), sizeof(BatchTile) * b->nbox, cudaMemcpyHostToDevice), "tables");
         b->ttotal[L] = first;
+        // 64 x 64 tiles for the 16-byte transpose
+        bool ok = true;
+        long long first4 = 0;
+        for (int k = 0; k < b->nbox; ++k) {
+            BatchTile &T = tt[k];
+            ok = ok && T.nr % 4 == 0 && T.nc % 4 == 0 && T.off % 4 == 0;
+            T.tr = (T.nr + 63) / 64;
+            T.tc = (T.nc + 63) / 64;
+            T.first = first4;
+            first4 += (long long)T.tr * T.tc * T.nz;
+        }
+        if (!b->ttiles4[L] && !(b->ttiles4[L] = (BatchTile *)balloc(b, sizeof(BatchTile) * b->nbox)))
+            return bfail(b, FISH_ERR_OOM, "batch table allocation failed");
+        FISH_BCK(b, cudaMemcpy(b->ttiles4[L], tt.data(), sizeof(BatchTile) * b->nbox, cudaMemcpyHostToDevice),
+                 "tables");
+        b->ttotal4[L] = first4;
+#ifdef FISH_TR_SCALAR
+        ok = false;
+#endif
+        b->t4 = (L == 0 ? ok : (b->t4 && ok));
     }
     // field pointer tables of the transposes, one per buffer parity
     for (int cu = 0; cu < 2; ++cu)
@@ -420,10 +510,18 @@ int batch_transpose(fish_batch *b)
 {
     // field pointers of the current and the other buffers (table by parity)
     const float **dsrc = b->tsrc + (b->cu * 2 + b->cb) * 16;
-    const long long nblk = b->ttotal[b->layout];
-    dim3 grid((unsigned)std::min<long long>(nblk, 1 << 30), (unsigned)((nblk + (1 << 30) - 1) / (1 << 30)));
-    transpose_batch_kernel<<<grid, dim3(32, 8), 0, b->stream>>>(dsrc, (float *const *)(dsrc + 8),
-                                                                b->ttiles[b->layout], b->nbox);
+    // (the field arrays come from the allocator, 256-byte aligned)
+    if (b->t4) {
+        const long long nblk = b->ttotal4[b->layout];
+        dim3 grid((unsigned)std::min<long long>(nblk, 1 << 30), (unsigned)((nblk + (1 << 30) - 1) / (1 << 30)));
+        transpose4_batch_kernel<<<grid, 256, 0, b->stream>>>(dsrc, (float *const *)(dsrc + 8), b->ttiles4[b->layout],
+                                                             b->nbox);
+    } else {
+        const long long nblk = b->ttotal[b->layout];
+        dim3 grid((unsigned)std::min<long long>(nblk, 1 << 30), (unsigned)((nblk + (1 << 30) - 1) / (1 << 30)));
+        transpose_batch_kernel<<<grid, dim3(32, 8), 0, b->stream>>>(dsrc, (float *const *)(dsrc + 8),
+                                                                    b->ttiles[b->layout], b->nbox);
+    }
     FISH_BCK(b, cudaGetLastError(), "batch transpose launch");
     b->cu = 1 - b->cu;
     b->cb = 1 - b->cb;
@@ -592,7 +690,9 @@ int fish_batch_create(int nbox, const int *dims, const double *gamma, const int 
                 if (!(h[3 * k + a] > 0.0)) return FISH_ERR_ARG;
         total += (long long)dims[3 * k] * dims[3 * k + 1] * dims[3 * k + 2];
     }
-    if (total > (1ll << 31)) return FISH_ERR_ARG;
+    // every element index of the batch fits an int (the fluid sweeps index
+    // with int; margin for the prefetch lines past a box's last column)
+    if (total > (1ll << 31) - (1ll << 20)) return FISH_ERR_ARG;
     fish_batch *b = new (std::nothrow) fish_batch;
     if (!b) return FISH_ERR_OOM;
     b->nbox = nbox;
