@@ -239,7 +239,9 @@ enum {
     FISH_BATCH_OPT_LIMITER = 0, /* FISH_LIM_VANLEER (default) or FISH_LIM_MINMOD */
     FISH_BATCH_OPT_ORDER = 1,   /* work-item order: 0 box order, 1 longest first, 2 round robin */
     FISH_BATCH_OPT_GROUPS = 2,  /* column groups (128 threads) per work item: 1, 2, 4, 8 */
-    FISH_BATCH_OPT_GRID = 3     /* persistent grid = SMs x resident blocks x (1, 2 or 4) */
+    FISH_BATCH_OPT_GRID = 3,    /* persistent grid = SMs x resident blocks x (1, 2 or 4) */
+    FISH_BATCH_OPT_CTROWS = 4   /* tile height of the constrained-transport sweeps: rows (warps) of
+                                   31 columns per work-item group, 4 (default) or 8 */
 };
 
 /* nbox boxes: dims[3k..3k+2] = nx, ny, nz of box k, gamma[k] > 1, bc[k]

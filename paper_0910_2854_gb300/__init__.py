@@ -29,7 +29,7 @@ FISH_LIM_VANLEER, FISH_LIM_MINMOD, FISH_LIM_NONE, FISH_LIM_HYBRID = 0, 1, 2, 3
 FISH_GRAV_UNSPLIT, FISH_GRAV_SPLIT = 0, 1
 FISH_F64, FISH_F32 = 0, 1
 FISH_OP_FLUID, FISH_OP_CT = 0, 1
-FISH_BATCH_OPT_LIMITER, FISH_BATCH_OPT_ORDER, FISH_BATCH_OPT_GROUPS, FISH_BATCH_OPT_GRID = range(4)
+FISH_BATCH_OPT_LIMITER, FISH_BATCH_OPT_ORDER, FISH_BATCH_OPT_GROUPS, FISH_BATCH_OPT_GRID, FISH_BATCH_OPT_CTROWS = range(5)
 
 # every symbol include/fish.h declares (checked by the CPU test suite)
 EXPORTS = ("fish_create", "fish_set_option", "fish_set_stream", "fish_set_allocator", "fish_set_state",

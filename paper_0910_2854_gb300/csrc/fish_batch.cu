@@ -86,8 +86,10 @@ __global__ void __launch_bounds__(128, FISH_COL_MINB)
     }
 }
 
-template <int LIM>
-__global__ void __launch_bounds__(128, FISH_CT_MINB)
+// ROWS: warps per work-item group, each on one of ROWS consecutive rows of a
+// segment (the tile height; blocks of 32 * ROWS threads)
+template <int LIM, int ROWS>
+__global__ void __launch_bounds__(32 * ROWS, FISH_CT_MINB * 4 / ROWS)
     ct_batch_kernel(const ColCTArgs<float> A, const BatchBox *__restrict__ boxes,
                     const BatchItem *__restrict__ items, int nitems, int *counter, const double *dt)
 {
@@ -112,12 +114,12 @@ __global__ void __launch_bounds__(128, FISH_CT_MINB)
         Ab.hf = B.hf;
         Ab.ho = B.ho;
         Ab.dt = dt + B.box;
-        // a group of four warps takes one segment of four consecutive rows
+        // a group of ROWS warps takes one segment of ROWS consecutive rows
         // (neighbour-row loads served from L1, as in the single-box kernel)
         const long long nseg = (Ab.nf + 30) / 31;
         for (int g = 0; g < I.groups; ++g) {
-            const long long q = (long long)I.first / 4 + g;
-            const long long ob = (q / nseg) * 4 + (threadIdx.x >> 5);
+            const long long q = (long long)I.first / ROWS + g;
+            const long long ob = (q / nseg) * ROWS + (threadIdx.x >> 5);
             ct_columns<float, LIM, true>(Ab, ob * nseg + q % nseg, threadIdx.x & 31);
         }
     }
@@ -280,6 +282,7 @@ struct fish_batch {
     int order = 0;                // 0 box order, 1 longest work first, 2 interleaved
     int groups = 1;               // column groups per work item
     int grid_factor = 1;          // persistent grid = SMs * resident blocks * factor
+    int ctrows = 4;               // constrained-transport rows (warps) per work-item group
 
     cudaStream_t own = nullptr, stream = nullptr;
     float *fl[2][5] = {};
@@ -402,10 +405,11 @@ int build_tables(fish_batch *b)
                 BatchItem I{k, (int)(g0 * 128), (int)std::min<long long>(b->groups, fgroups - g0)};
                 fw.push_back({(long long)B.n * I.groups, I});
             }
-            // 31 columns per warp; a group is one segment of four rows
-            const long long cgroups = (long long)((B.nf + 30) / 31) * ((B.no + 3) / 4);
+            // 31 columns per warp; a group is one segment of ctrows rows
+            const int R = b->ctrows;
+            const long long cgroups = (long long)((B.nf + 30) / 31) * ((B.no + R - 1) / R);
             for (long long g0 = 0; g0 < cgroups; g0 += b->groups) {
-                BatchItem I{k, (int)(g0 * 4), (int)std::min<long long>(b->groups, cgroups - g0)};
+                BatchItem I{k, (int)(g0 * R), (int)std::min<long long>(b->groups, cgroups - g0)};
                 cw.push_back({(long long)B.n * I.groups, I});
             }
         }
@@ -593,12 +597,22 @@ int batch_ct(fish_batch *b, int d, int counter)
     A.boo = b->bf[1 - b->cb][other];
     A.lim = b->lim;
     int *ctr = b->counters + counter;
-    if (b->lim == FISH_LIM_VANLEER)
-        ct_batch_kernel<LIM_VANLEER><<<b->ct_blocks, 128, 0, b->stream>>>(A, b->boxes[d], b->citems[d],
-                                                                        b->ncitems[d], ctr, b->dt);
-    else
-        ct_batch_kernel<LIM_MINMOD><<<b->ct_blocks, 128, 0, b->stream>>>(A, b->boxes[d], b->citems[d],
-                                                                       b->ncitems[d], ctr, b->dt);
+    const bool vl = b->lim == FISH_LIM_VANLEER;
+    if (b->ctrows == 8) {
+        if (vl)
+            ct_batch_kernel<LIM_VANLEER, 8><<<b->ct_blocks, 256, 0, b->stream>>>(A, b->boxes[d], b->citems[d],
+                                                                               b->ncitems[d], ctr, b->dt);
+        else
+            ct_batch_kernel<LIM_MINMOD, 8><<<b->ct_blocks, 256, 0, b->stream>>>(A, b->boxes[d], b->citems[d],
+                                                                              b->ncitems[d], ctr, b->dt);
+    } else {
+        if (vl)
+            ct_batch_kernel<LIM_VANLEER, 4><<<b->ct_blocks, 128, 0, b->stream>>>(A, b->boxes[d], b->citems[d],
+                                                                               b->ncitems[d], ctr, b->dt);
+        else
+            ct_batch_kernel<LIM_MINMOD, 4><<<b->ct_blocks, 128, 0, b->stream>>>(A, b->boxes[d], b->citems[d],
+                                                                              b->ncitems[d], ctr, b->dt);
+    }
     FISH_BCK(b, cudaGetLastError(), "batch constrained-transport launch");
     b->cb = 1 - b->cb;
     b->launches += 1;
@@ -760,6 +774,10 @@ int fish_batch_set_option(fish_batch *b, int key, double v)
         if (v != 1 && v != 2 && v != 4) return bfail(b, FISH_ERR_ARG, "grid factor: 1, 2 or 4");
         b->grid_factor = (int)v;
         break;
+    case FISH_BATCH_OPT_CTROWS:
+        if (v != 4 && v != 8) return bfail(b, FISH_ERR_ARG, "constrained-transport rows per item: 4 or 8");
+        b->ctrows = (int)v;
+        break;
     default:
         return bfail(b, FISH_ERR_ARG, "unknown batch option");
     }
@@ -828,8 +846,12 @@ int fish_batch_step(fish_batch *b, double k, int nsteps)
         int occ_f = 0, occ_c = 0;
         FISH_BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, fluid_batch_kernel<LIM_VANLEER, true>, 128, 0),
                  "occupancy");
-        FISH_BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, ct_batch_kernel<LIM_VANLEER>, 128, 0),
-                 "occupancy");
+        if (b->ctrows == 8)
+            FISH_BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, ct_batch_kernel<LIM_VANLEER, 8>, 256, 0),
+                     "occupancy");
+        else
+            FISH_BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_c, ct_batch_kernel<LIM_VANLEER, 4>, 128, 0),
+                     "occupancy");
         b->fluid_blocks = std::max(1, occ_f) * b->sms * b->grid_factor;
         b->ct_blocks = std::max(1, occ_c) * b->sms * b->grid_factor;
         cudaGraph_t graph = nullptr;

@@ -219,7 +219,7 @@ def batch(k=0.5, steps=10):
     ms = e0.elapsed_time(e1) / steps
     out = {"report": "batch", "boxes": len(ws), "cells": b.cells, "ms_per_step": ms,
            "cell_updates_per_s": b.cells / (ms * 1e-3), "launches_per_step": 15,
-           "tuning": {kk: choice[kk] for kk in ("order", "groups", "grid")}}
+           "tuning": dict({kk: choice[kk] for kk in ("order", "groups", "grid")}, ctrows=choice.get("ctrows", 4))}
     b.close()
     return out
 

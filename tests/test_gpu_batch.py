@@ -104,11 +104,12 @@ def test_batch_tuning_options_do_not_change_results(F):
     ref.step(0.5, 2)
     want = [ref.get_state(i) for i in range(len(ws))]
     ref.close()
-    for order, groups, grid in ((1, 2, 1), (2, 4, 2), (0, 8, 4)):
+    for order, groups, grid, rows in ((1, 2, 1, 4), (2, 4, 2, 8), (0, 8, 4, 8), (0, 1, 1, 8)):
         b = make_batch(F, ws)
         b.set_option(F.FISH_BATCH_OPT_ORDER, order)
         b.set_option(F.FISH_BATCH_OPT_GROUPS, groups)
         b.set_option(F.FISH_BATCH_OPT_GRID, grid)
+        b.set_option(F.FISH_BATCH_OPT_CTROWS, rows)
         b.step(0.5, 2)
         for i in range(len(ws)):
             assert np.array_equal(b.get_state(i), want[i]), (order, groups, grid, i)
