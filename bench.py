@@ -69,6 +69,9 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--kernels", default="column", choices=("column", "ring"),
+                   help="kernel family of the FP32 fluid sweep: register-prefetch column march (default) or the "
+                        "march fed through a shared-memory ring of TMA bulk copies")
     p.add_argument("--decomp", action="store_true",
                    help="one box split into z-slabs over the ranks (halo exchange, strong scaling) instead of one "
                         "box per rank")
@@ -219,7 +222,7 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def make_box(F, W, spec, n, torch):
+def make_box(F, W, spec, n, torch, kernels="column"):
     prec = spec["precision"]
     dt_ = torch.float32 if prec == "fp32" else torch.float64
     if spec is WORKLOAD:
@@ -228,7 +231,7 @@ def make_box(F, W, spec, n, torch):
     else:
         w = W.orszag_tang(n)
         st = torch.as_tensor(w.state, device="cuda", dtype=dt_)
-    box = F.Box(n, n, n, w.gamma, precision=prec, h=w.h)
+    box = F.Box(n, n, n, w.gamma, precision=prec, h=w.h, kernels=kernels)
     box.set_state(st)
     del st, w
     torch.cuda.empty_cache()
@@ -331,7 +334,7 @@ def run_fish(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     n = args.n or WORKLOAD["n"]
-    box = make_box(F, W, WORKLOAD, n, torch)
+    box = make_box(F, W, WORKLOAD, n, torch, args.kernels)
     clocks = ClockSampler(local)
 
     def barrier():
@@ -435,7 +438,8 @@ def run_fish(args, rank, world, local):
                   "config": {"workload": WORKLOAD["workload"], "cells": n ** 3, "cfl": CFL,
                              "parallelism": "replicas x%d (one box per GPU, no data-path collective)" % world,
                              "l2": "inputs larger than L2 (34 GB state vs 129 MB L2)",
-                             "graph": "one CUDA graph per double step (CFL + 12 sweeps)"},
+                             "graph": "one CUDA graph per double step (CFL + 12 sweeps)",
+                             "fluid_kernels": args.kernels},
                   "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                   "clocks": clk, "fp64_path": fp64, "batch": batch}
     else:
