@@ -413,6 +413,8 @@ template <class V> struct FMarch {
     V phm2;              // potential of raw cell r-2
     Checks<V> chk;
     V cflr;              // largest CFL rate of the output cells (CFLF)
+    V *bbs;              // CFLF: the thread's ring of cell-centred fields of raw cells r .. r-3 in
+                         // shared memory (slot r mod 4, component k at [(slot*3 + k) * 128])
     typename VT<V>::S w0, w1, w2, w3, w4;  // irregular mesh: widths of raw cells r, r-1, .. r-4
     V dprev;             // split gravity: potential (FP64) or its difference (FP32) of raw cell r-1
 };
@@ -583,6 +585,10 @@ __device__ __forceinline__ V sg_image_dk(const ColFluidArgs<typename VT<V>::S> &
 // operator-split kicks G_d(dt/2) folded into the march (eq025111): the raw
 // cell is kicked as it is consumed, the output cell's old state before its
 // update and the result after it (reading C-22 for the kick).
+#ifndef FISH_CFL_SMEM
+#define FISH_CFL_SMEM 1   // CFL epilogue: cell-centred field from a shared-memory ring
+#endif
+
 template <class V, bool HSE, int GM, int LIM, bool FT1, bool CFLF, bool NU, int K, int ST, int LD, class IX = long long>
 __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S, IX> &X,
                                       FMarch<V> &M, int r, V lam, V lamh, V hdt, V dt, V rtwoh,
@@ -608,6 +614,12 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
         bbr[2] = bfc;
     }
     const V phr = PHI ? M.R.phi : vb<V>(0.0f);  // no potential: phi = 0
+    if constexpr (CFLF && FISH_CFL_SMEM) {
+        // keep the cell-centred field of raw cell r for the CFL rate of its
+        // update three steps later (b is unchanged by L_d)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) M.bbs[((K & 3) * 3 + k) * 128] = bbr[k];
+    }
     if constexpr (NU) {
         M.w4 = M.w3;
         M.w3 = M.w2;
@@ -728,17 +740,24 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
 #pragma unroll
                 for (int k = 0; k < 5; ++k) vstore(A.uo[k], io, un[k]);
                 if constexpr (CFLF) {
-                    // CFL rate of the updated cell with its cell-centred field
-                    const auto *bfp = FT1 ? A.bt1 : A.bt2;
-                    const auto *bop = FT1 ? A.bt2 : A.bt1;
-                    const IX iom = X.base + (IX)(o > 0 ? o - 1 : gmap(-1, A.n, A.bc)) * (IX)A.sd;
+                    // CFL rate of the updated cell with its cell-centred field,
+                    // formed when the cell entered as raw cell o = r-3 (slot
+                    // (r-3) mod 4 of the ring)
                     V bc[3];
-                    bc[0] = half * (vload<V>(A.bd, iom) + vload<V>(A.bd, io));
-                    const V bfv = vload<V>(bfp, io);
-                    const V bfc = half * (vshift_lo(__ldg(bfp + io + X.ofm), bfv) + bfv);
-                    const V boc = half * (vload<V>(bop, io + X.oom) + vload<V>(bop, io));
-                    bc[FT1 ? 1 : 2] = bfc;
-                    bc[FT1 ? 2 : 1] = boc;
+                    if constexpr (FISH_CFL_SMEM) {
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) bc[k] = M.bbs[(((K + 1) & 3) * 3 + k) * 128];
+                    } else {
+                        const auto *bfp = FT1 ? A.bt1 : A.bt2;
+                        const auto *bop = FT1 ? A.bt2 : A.bt1;
+                        const IX iom = X.base + (IX)(o > 0 ? o - 1 : gmap(-1, A.n, A.bc)) * (IX)A.sd;
+                        bc[0] = half * (vload<V>(A.bd, iom) + vload<V>(A.bd, io));
+                        const V bfv = vload<V>(bfp, io);
+                        const V bfc = half * (vshift_lo(__ldg(bfp + io + X.ofm), bfv) + bfv);
+                        const V boc = half * (vload<V>(bop, io + X.oom) + vload<V>(bop, io));
+                        bc[FT1 ? 1 : 2] = bfc;
+                        bc[FT1 ? 2 : 1] = boc;
+                    }
                     const V rh[3] = {vb<V>(A.rh[0]), vb<V>(A.rh[1]), vb<V>(A.rh[2])};
                     M.cflr = vmax(M.cflr, cfl_rate3<V>(un, bc, vb<V>(A.gamma), vb<V>(A.gm1), rh));
                 }
@@ -811,6 +830,11 @@ __device__ __forceinline__ void fluid_columns(const ColFluidArgs<typename VT<V>:
     const int n = A.n;
 
     FMarch<V> M;
+    if constexpr (CFLF && FISH_CFL_SMEM) {
+        static_assert(VT<V>::W == 2, "the CFL epilogue is built for the packed kernels");
+        __shared__ V cfl_bb[4 * 3 * 128];  // blocks of 128 threads
+        M.bbs = cfl_bb + (threadIdx.x & 127);
+    }
     checks_init(M.chk);
     M.cflr = vb<V>(0.0f);
     M.phm2 = vb<V>(0.0f);
