@@ -47,6 +47,21 @@ WORKLOAD = {
     "precision": "fp32",
     "gamma": 5.0 / 3.0,
 }
+
+
+def workload_name(n):
+    """The workload's description at n^3 cells (1024^3 is the timed box)."""
+    return WORKLOAD["workload"].replace("1024^3", "%d^3" % n)
+
+
+def l2_note(n):
+    """Whether one copy of the FP32 state (32 B per cell) exceeds the 129 MB L2."""
+    gb = 32.0 * n ** 3 / 1e9
+    if gb * 1e3 > 129.0:
+        return "inputs larger than L2 (%.3g GB state vs 129 MB L2)" % gb
+    return "inputs fit in L2 (%.3g MB state vs 129 MB L2): small test size, not a timing configuration" % (gb * 1e3)
+
+
 FP64_WORKLOAD = {
     "workload": "3D Orszag-Tang-type vortex 256^3 periodic, FP64 (plain method)",
     "n": 256,
@@ -404,8 +419,8 @@ def run_fish(args, rank, world, local):
                 from paper_0910_2854_gb300 import reports
                 sb = reports.fp32_vs_fp64(n, steps=3, k=CFL)
                 fp64["same_box"] = {
-                    "workload": WORKLOAD["workload"].replace("FP32 bulk with compensated pressure recovery and "
-                                                             "FP64 reductions", "FP64 throughout"),
+                    "workload": workload_name(n).replace("FP32 bulk with compensated pressure recovery and "
+                                                         "FP64 reductions", "FP64 throughout"),
                     "fp64_ms_per_step": sb["fp64"]["ms_per_step"], "fp64_value": sb["fp64"]["cell_updates_per_s"],
                     "fp32_over_fp64": (value / world) / sb["fp64"]["cell_updates_per_s"],
                     "l1_rho_rel_fp32_vs_fp64": sb["l1_rho_rel"], "steps_compared": 3}
@@ -435,9 +450,9 @@ def run_fish(args, rank, world, local):
         result = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                   "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                   "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded, generated on the device)",
-                  "config": {"workload": WORKLOAD["workload"], "cells": n ** 3, "cfl": CFL,
+                  "config": {"workload": workload_name(n), "cells": n ** 3, "cfl": CFL,
                              "parallelism": "replicas x%d (one box per GPU, no data-path collective)" % world,
-                             "l2": "inputs larger than L2 (34 GB state vs 129 MB L2)",
+                             "l2": l2_note(n),
                              "graph": "one CUDA graph per double step (CFL + 12 sweeps)",
                              "fluid_kernels": args.kernels},
                   "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
@@ -513,10 +528,10 @@ def run_fish_decomp(args, rank, world, local):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "strong",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded, generated on the device)",
-                "config": {"workload": WORKLOAD["workload"], "cells": n ** 3, "cfl": CFL,
+                "config": {"workload": workload_name(n), "cells": n ** 3, "cfl": CFL,
                            "parallelism": "z-slabs x%d (%d ghost planes exchanged before every operator, "
                                           "all-reduced CFL step)" % (world, decomp.HALO),
-                           "l2": "inputs larger than L2"},
+                           "l2": l2_note(n)},
                 "roofline": {"bound": "hbm", "achieved": per_gpu, "peak": peak, "unit": "GB/s",
                              "frac": per_gpu / peak, "traffic": None,
                              "kernel": "whole double step per GPU (384 B/cell floor)", "peak_source": peak_kind},
