@@ -18,9 +18,3 @@ def job_throughput(ms_local, cells_local, device="cpu"):
     dist.all_reduce(c, op=dist.ReduceOp.SUM)
     return c.item() / (t.item() * 1e-3), t.item()
 
-
-def replica_seed(base_seed, rank):
-    """Seed of a rank's box: every replica advances the same seeded workload
-    (weak scaling, identical work per GPU); kept as a function so a run with
-    distinct boxes per rank only changes this line."""
-    return base_seed
