@@ -63,6 +63,10 @@ cudaError_t col_fluid_launch(const ColFluidArgs<typename VT<V>::S> &A, cudaStrea
     return cudaGetLastError();
 }
 
+#ifndef FISH_F64_VL
+#define FISH_F64_VL 1   // FP64 sweeps without gravity: compile-time Van Leer limiter
+#endif
+
 // GRAV: 0 no potential, 1 unsplit source terms, 2 split kicks in the march
 // (uniform meshes; with an irregular mesh the kicks run as separate passes)
 template <class V, bool HSE, int GRAV, bool FT1>
@@ -88,6 +92,10 @@ static cudaError_t col_fluid_lim(const ColFluidArgs<typename VT<V>::S> &A, cudaS
         // irregular mesh: widths along d (limiter read at run time)
         if constexpr (GRAV != 2) {
             if (A.wd) return col_fluid_launch<V, HSE, GRAV, -1, FT1, true>(A, s);
+        }
+        if constexpr (VT<V>::F64 && !HSE && GRAV == 0 && FISH_F64_VL) {
+            // the plain FP64 sweeps with a compile-time Van Leer limiter
+            if (A.lim == LIM_VANLEER) return col_fluid_launch<V, HSE, GRAV, LIM_VANLEER, FT1>(A, s);
         }
         if constexpr (HSE && std::is_same<V, float>::value) {
             // the hydrostatic sweeps (one column per thread): compile-time
@@ -147,6 +155,8 @@ template <class V> cudaError_t col_ct(const ColCTArgs<typename VT<V>::S> &A, boo
     if (nu && (!A.wf || !A.wo)) return cudaErrorInvalidValue;
     if constexpr (VT<V>::F64) {
         if (nu) return ft1 ? col_ct_launch<V, -1, true, true>(A, s) : col_ct_launch<V, -1, false, true>(A, s);
+        if (FISH_F64_VL && A.lim == LIM_VANLEER)
+            return ft1 ? col_ct_launch<V, LIM_VANLEER, true>(A, s) : col_ct_launch<V, LIM_VANLEER, false>(A, s);
         return ft1 ? col_ct_launch<V, -1, true>(A, s) : col_ct_launch<V, -1, false>(A, s);
     } else if constexpr (std::is_same<V, P2>::value) {
         if (nu) return cudaErrorInvalidValue;

@@ -16,6 +16,9 @@ FISH_F64_T2(true, 1, false)
 FISH_F64_T2(true, 1, true)
 FISH_F64_T2(false, 2, false)
 #undef FISH_F64_T2
+template cudaError_t col_fluid_launch<double, false, 0, LIM_VANLEER, false, false>(const ColFluidArgs<double> &,
+                                                                                 cudaStream_t);
+template cudaError_t col_ct_launch<double, LIM_VANLEER, false, false>(const ColCTArgs<double> &, cudaStream_t);
 template cudaError_t col_ct_launch<double, -1, false, false>(const ColCTArgs<double> &, cudaStream_t);
 template cudaError_t col_ct_launch<double, -1, false, true>(const ColCTArgs<double> &, cudaStream_t);
 }
