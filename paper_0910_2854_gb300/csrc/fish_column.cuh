@@ -589,7 +589,8 @@ __device__ __forceinline__ V sg_image_dk(const ColFluidArgs<typename VT<V>::S> &
 #define FISH_CFL_SMEM 1   // CFL epilogue: cell-centred field from a shared-memory ring
 #endif
 
-template <class V, bool HSE, int GM, int LIM, bool FT1, bool CFLF, bool NU, int K, int ST, int LD, class IX = long long>
+template <class V, bool HSE, int GM, int LIM, bool FT1, bool CFLF, bool NU, int K, int ST, int LD, class IX = long long,
+          bool PFW = FISH_FL_PF_WARP != 0>
 __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, const FCtx<typename VT<V>::S, IX> &X,
                                       FMarch<V> &M, int r, V lam, V lamh, V hdt, V dt, V rtwoh,
                                       const FPf<typename VT<V>::S, IX> &PF)
@@ -634,7 +635,7 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
         M.R.bdm = bd_r;
         if constexpr (LD == LD_DIRECT_PF) {
             const int pf = min(r + 1 + FISH_PF_DIST, A.n - 1);
-            if constexpr (FISH_FL_PF_WARP) fpf_step(A, PF, pf);
+            if constexpr (PFW) fpf_step(A, PF, pf);
             else fprefetch<V, PHI, FT1, IX>(A, X, X.base + (IX)pf * (IX)A.sd);
         }
     } else if constexpr (LD == LD_MAPPED) {
@@ -776,17 +777,18 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
 
 // L_d over all columns.  The prologue runs raw cells -3 .. 2 (K = 1, 2, 3,
 // 0, 1, 2); boxes with n < 8 load everything through the map.
-template <class V, bool HSE, int GRAV, int LIM, bool FT1, bool CFLF, bool NU, int PLD, class IX = long long>
+template <class V, bool HSE, int GRAV, int LIM, bool FT1, bool CFLF, bool NU, int PLD, class IX = long long,
+          bool PFW = FISH_FL_PF_WARP != 0>
 __device__ __forceinline__ void fprologue(const ColFluidArgs<typename VT<V>::S> &A,
                                           const FCtx<typename VT<V>::S, IX> &X, FMarch<V> &M, V lam, V lamh, V hdt,
                                           V dt, V rtwoh, const FPf<typename VT<V>::S, IX> &PF)
 {
-    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, 0, LD_MAPPED, IX>(A, X, M, -3, lam, lamh, hdt, dt, rtwoh, PF);
-    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ST_F1, LD_MAPPED, IX>(A, X, M, -2, lam, lamh, hdt, dt, rtwoh, PF);
-    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ST_F1 | ST_PRED, PLD, IX>(A, X, M, -1, lam, lamh, hdt, dt, rtwoh, PF);
-    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ST_F1 | ST_PRED, PLD, IX>(A, X, M, 0, lam, lamh, hdt, dt, rtwoh, PF);
-    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ST_F1 | ST_PRED, PLD, IX>(A, X, M, 1, lam, lamh, hdt, dt, rtwoh, PF);
-    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ST_F1 | ST_PRED | ST_F2, PLD, IX>(A, X, M, 2, lam, lamh, hdt, dt, rtwoh, PF);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, 0, LD_MAPPED, IX, PFW>(A, X, M, -3, lam, lamh, hdt, dt, rtwoh, PF);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ST_F1, LD_MAPPED, IX, PFW>(A, X, M, -2, lam, lamh, hdt, dt, rtwoh, PF);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ST_F1 | ST_PRED, PLD, IX, PFW>(A, X, M, -1, lam, lamh, hdt, dt, rtwoh, PF);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ST_F1 | ST_PRED, PLD, IX, PFW>(A, X, M, 0, lam, lamh, hdt, dt, rtwoh, PF);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ST_F1 | ST_PRED, PLD, IX, PFW>(A, X, M, 1, lam, lamh, hdt, dt, rtwoh, PF);
+    fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ST_F1 | ST_PRED | ST_F2, PLD, IX, PFW>(A, X, M, 2, lam, lamh, hdt, dt, rtwoh, PF);
 }
 
 #ifndef FISH_COL_MINB
@@ -797,7 +799,12 @@ __device__ __forceinline__ void fprologue(const ColFluidArgs<typename VT<V>::S> 
 #endif
 
 // The march of thread cid (column group cid of the box described by A).
-template <class V, bool HSE, int GRAV, int LIM, bool FT1, bool CFLF, bool NU = false, class IX = long long>
+// PFW: L2 prefetch of the next cells by one instruction per warp over the
+// warp's span of its first row (the single-box sweeps, whose rows hold a
+// multiple of 32 column groups), or per lane and field (the batch, whose
+// short rows leave warps that straddle two rows)
+template <class V, bool HSE, int GRAV, int LIM, bool FT1, bool CFLF, bool NU = false, class IX = long long,
+          bool PFW = FISH_FL_PF_WARP != 0>
 __device__ __forceinline__ void fluid_columns(const ColFluidArgs<typename VT<V>::S> &A, long long cid)
 {
     using S = typename VT<V>::S;
@@ -813,7 +820,8 @@ __device__ __forceinline__ void fluid_columns(const ColFluidArgs<typename VT<V>:
     // per-warp L2 prefetch over the span of the warp's first lane (32 groups
     // of W columns; a warp that crosses a row end prefetches its first row)
     FPf<S, IX> PF;
-    {
+    PF.p = nullptr;
+    if constexpr (PFW) {
         const unsigned am = __activemask();
         const int l0 = __ffs(am) - 1;
         const IX b0 = __shfl_sync(am, X.base, l0);
@@ -845,27 +853,27 @@ __device__ __forceinline__ void fluid_columns(const ColFluidArgs<typename VT<V>:
     constexpr int ALL = ST_F1 | ST_PRED | ST_F2 | ST_OUT;
     int r = 3;
     if (n >= 8) {
-        fprologue<V, HSE, GRAV, LIM, FT1, CFLF, NU, LD_DIRECT, IX>(A, X, M, lam, lamh, hdt, dt, rtwoh, PF);
+        fprologue<V, HSE, GRAV, LIM, FT1, CFLF, NU, LD_DIRECT, IX, PFW>(A, X, M, lam, lamh, hdt, dt, rtwoh, PF);
         // steady state: the four steps r .. r+3 prefetch interior cells
 #pragma unroll 1
         for (; r + 4 <= n - 1; r += 4) {
-            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ALL, LD_DIRECT_PF, IX>(A, X, M, r, lam, lamh, hdt, dt, rtwoh, PF);
-            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ALL, LD_DIRECT_PF, IX>(A, X, M, r + 1, lam, lamh, hdt, dt, rtwoh, PF);
-            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ALL, LD_DIRECT_PF, IX>(A, X, M, r + 2, lam, lamh, hdt, dt, rtwoh, PF);
-            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ALL, LD_DIRECT_PF, IX>(A, X, M, r + 3, lam, lamh, hdt, dt, rtwoh, PF);
+            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ALL, LD_DIRECT_PF, IX, PFW>(A, X, M, r, lam, lamh, hdt, dt, rtwoh, PF);
+            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ALL, LD_DIRECT_PF, IX, PFW>(A, X, M, r + 1, lam, lamh, hdt, dt, rtwoh, PF);
+            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ALL, LD_DIRECT_PF, IX, PFW>(A, X, M, r + 2, lam, lamh, hdt, dt, rtwoh, PF);
+            fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ALL, LD_DIRECT_PF, IX, PFW>(A, X, M, r + 3, lam, lamh, hdt, dt, rtwoh, PF);
         }
     } else {
-        fprologue<V, HSE, GRAV, LIM, FT1, CFLF, NU, LD_MAPPED, IX>(A, X, M, lam, lamh, hdt, dt, rtwoh, PF);
+        fprologue<V, HSE, GRAV, LIM, FT1, CFLF, NU, LD_MAPPED, IX, PFW>(A, X, M, lam, lamh, hdt, dt, rtwoh, PF);
     }
     // tail: raw cells r .. n+2 (r = 3 mod 4, at most seven), loads through
     // the map (harmless beyond n+2)
-    if (r <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ALL, LD_MAPPED, IX>(A, X, M, r, lam, lamh, hdt, dt, rtwoh, PF);
-    if (r + 1 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ALL, LD_MAPPED, IX>(A, X, M, r + 1, lam, lamh, hdt, dt, rtwoh, PF);
-    if (r + 2 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ALL, LD_MAPPED, IX>(A, X, M, r + 2, lam, lamh, hdt, dt, rtwoh, PF);
-    if (r + 3 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ALL, LD_MAPPED, IX>(A, X, M, r + 3, lam, lamh, hdt, dt, rtwoh, PF);
-    if (r + 4 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ALL, LD_MAPPED, IX>(A, X, M, r + 4, lam, lamh, hdt, dt, rtwoh, PF);
-    if (r + 5 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ALL, LD_MAPPED, IX>(A, X, M, r + 5, lam, lamh, hdt, dt, rtwoh, PF);
-    if (r + 6 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ALL, LD_NONE, IX>(A, X, M, r + 6, lam, lamh, hdt, dt, rtwoh, PF);
+    if (r <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ALL, LD_MAPPED, IX, PFW>(A, X, M, r, lam, lamh, hdt, dt, rtwoh, PF);
+    if (r + 1 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ALL, LD_MAPPED, IX, PFW>(A, X, M, r + 1, lam, lamh, hdt, dt, rtwoh, PF);
+    if (r + 2 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ALL, LD_MAPPED, IX, PFW>(A, X, M, r + 2, lam, lamh, hdt, dt, rtwoh, PF);
+    if (r + 3 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 2, ALL, LD_MAPPED, IX, PFW>(A, X, M, r + 3, lam, lamh, hdt, dt, rtwoh, PF);
+    if (r + 4 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 3, ALL, LD_MAPPED, IX, PFW>(A, X, M, r + 4, lam, lamh, hdt, dt, rtwoh, PF);
+    if (r + 5 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 0, ALL, LD_MAPPED, IX, PFW>(A, X, M, r + 5, lam, lamh, hdt, dt, rtwoh, PF);
+    if (r + 6 <= n + 2) fstep<V, HSE, GRAV, LIM, FT1, CFLF, NU, 1, ALL, LD_NONE, IX, PFW>(A, X, M, r + 6, lam, lamh, hdt, dt, rtwoh, PF);
     const unsigned fl = checks_flags(M.chk);
     if (fl) atomicOr(A.flags, fl);
     if constexpr (CFLF) {
