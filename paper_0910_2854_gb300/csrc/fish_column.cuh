@@ -413,8 +413,6 @@ template <class V> struct FMarch {
     V phm2;              // potential of raw cell r-2
     Checks<V> chk;
     V cflr;              // largest CFL rate of the output cells (CFLF)
-    V *bbs;              // CFLF: the thread's ring of cell-centred fields of raw cells r .. r-3 in
-                         // shared memory (slot r mod 4, component k at [(slot*3 + k) * 128])
     typename VT<V>::S w0, w1, w2, w3, w4;  // irregular mesh: widths of raw cells r, r-1, .. r-4
     V dprev;             // split gravity: potential (FP64) or its difference (FP32) of raw cell r-1
 };
@@ -588,6 +586,11 @@ __device__ __forceinline__ V sg_image_dk(const ColFluidArgs<typename VT<V>::S> &
 #ifndef FISH_CFL_SMEM
 #define FISH_CFL_SMEM 1   // CFL epilogue: cell-centred field from a shared-memory ring
 #endif
+// The ring of the packed kernels with the CFL epilogue (blocks of 128
+// threads): the cell-centred fields of a thread's raw cells r .. r-3, slot
+// r mod 4, component k at [(slot * 3 + k) * 128 + thread]; only the kernels
+// that use it allocate it.
+static __shared__ float2 cfl_bb_ring[4 * 3 * 128];
 
 template <class V, bool HSE, int GM, int LIM, bool FT1, bool CFLF, bool NU, int K, int ST, int LD, class IX = long long,
           bool PFW = FISH_FL_PF_WARP != 0>
@@ -618,8 +621,10 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
     if constexpr (CFLF && FISH_CFL_SMEM) {
         // keep the cell-centred field of raw cell r for the CFL rate of its
         // update three steps later (b is unchanged by L_d)
+        static_assert(VT<V>::W == 2, "the CFL epilogue is built for the packed kernels");
+        const int t = threadIdx.x & 127;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) M.bbs[((K & 3) * 3 + k) * 128] = bbr[k];
+        for (int k = 0; k < 3; ++k) cfl_bb_ring[((K & 3) * 3 + k) * 128 + t] = bbr[k].v;
     }
     if constexpr (NU) {
         M.w4 = M.w3;
@@ -746,8 +751,9 @@ __device__ __forceinline__ void fstep(const ColFluidArgs<typename VT<V>::S> &A, 
                     // (r-3) mod 4 of the ring)
                     V bc[3];
                     if constexpr (FISH_CFL_SMEM) {
+                        const int t = threadIdx.x & 127;
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) bc[k] = M.bbs[(((K + 1) & 3) * 3 + k) * 128];
+                        for (int k = 0; k < 3; ++k) bc[k].v = cfl_bb_ring[(((K + 1) & 3) * 3 + k) * 128 + t];
                     } else {
                         const auto *bfp = FT1 ? A.bt1 : A.bt2;
                         const auto *bop = FT1 ? A.bt2 : A.bt1;
@@ -838,11 +844,6 @@ __device__ __forceinline__ void fluid_columns(const ColFluidArgs<typename VT<V>:
     const int n = A.n;
 
     FMarch<V> M;
-    if constexpr (CFLF && FISH_CFL_SMEM) {
-        static_assert(VT<V>::W == 2, "the CFL epilogue is built for the packed kernels");
-        __shared__ V cfl_bb[4 * 3 * 128];  // blocks of 128 threads
-        M.bbs = cfl_bb + (threadIdx.x & 127);
-    }
     checks_init(M.chk);
     M.cflr = vb<V>(0.0f);
     M.phm2 = vb<V>(0.0f);
