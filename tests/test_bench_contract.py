@@ -54,3 +54,15 @@ def test_gpu_decomposed_line():
     assert {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "scaling"} <= set(d)
     assert d["scaling"] == "strong" and d["value"] > 0 and d["gpu_launches"] > 0
     assert d["exchanges_per_step"] == 13
+
+
+def test_workload_names_follow_the_size():
+    """The config of a line names the box it ran and says whether one FP32
+    state copy exceeds the 129 MB L2 (1024^3: 34.4 GB; 128^3: 67 MB)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    assert "1024^3" in b.workload_name(1024) and "384^3" in b.workload_name(384)
+    assert b.l2_note(1024).startswith("inputs larger than L2") and "34.4 GB" in b.l2_note(1024)
+    assert b.l2_note(128).startswith("inputs fit in L2")
